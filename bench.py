@@ -1,0 +1,298 @@
+"""Benchmark of the fused coupled-LBM step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16] [--impl ours|reference]
+
+One step = one pass of the whole hot path (moments, stencils, closures, forces,
+the three collisions, streaming and boundary rules) over the 2048 x 512 bubble
+channel (two bubbles, Poiseuille inlet, outflow, parabolic sigma(T)), with the
+state resident in HBM.  Each timed step is bracketed by CUDA events on the
+lattice's stream; an L2 flush (a 256 MiB write) runs between timed steps,
+outside the events.  Metric: lattice updates per second (MLUPS, one update = one
+node through all three LBEs), whole job.  Prints one JSON line.
+
+N > 1 (torchrun, one rank per GPU): independent replicas (the path has no
+data-path exchange); value = all ranks' updates / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on this machine's host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 2048, 512
+WORKLOAD = "bubbles_2048x512"
+# algorithmic bytes per lattice update: every population read once and written once
+# (27 x 2 x element size) plus the previous (phi u) read and written (2 x 2 x 4 B)
+ALG_BYTES = {"fp32": 27 * 2 * 4 + 16, "fp16": 27 * 2 * 2 + 16}
+CPU_SAMPLE_SECONDS = 15.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_11320_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(storage):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "step_%s_%s.json" % (storage, WORKLOAD))
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernel_hash") == _kernel_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle_sample(seconds, threads=None):
+    """Time the FP64 oracle on the bubble workload for about `seconds` of CPU work."""
+    from oracle.oracle import OracleSim, num_threads, set_threads
+    from paper_2306_11320_gb300 import workloads as WL
+
+    if threads:
+        set_threads(threads)
+    params, fields, _ = WL.bubbles(nx=NX, ny=NY)
+    sim = OracleSim(NX, NY, params)
+    sim.init(**fields)
+    sim.step(1)  # first touch of every buffer
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and steps >= 2:
+            break
+    return NX * NY * steps / el / 1e6, steps, el, num_threads()
+
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    mlups, steps, el, cores = run_oracle_sample(per_step * max(1, args.steps))
+    line = {
+        "metric": "coupled-LBM MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "l2": "inputs > L2 (CPU run)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d oracle steps of the %dx%d bubble channel" % (steps, NX, NY)},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2306_11320_gb300 import workloads as WL
+    from paper_2306_11320_gb300.tpflbm import STORAGE_FP16, STORAGE_FP32, Lattice
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    storage = STORAGE_FP16 if args.storage == "fp16" else STORAGE_FP32
+    params, fields, _ = WL.bubbles(nx=NX, ny=NY)
+    if storage == STORAGE_FP16:
+        params.update(WL.fp16_scales(params))
+    stream = torch.cuda.Stream(device=dev)
+    lat = Lattice(NX, NY, params, storage=storage, stream=stream)
+    f32 = {k: v.astype(np.float32) for k, v in fields.items()}
+    lat.init(**f32)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lat.step(1)
+            flush.fill_(1)
+        barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with ClockSampler(local_rank) as clk:
+            for k in range(args.steps):
+                starts[k].record(stream)
+                lat.step(1)
+                ends[k].record(stream)
+                flush.fill_(1)
+            barrier()
+        times = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    diag = lat.diagnostics()
+
+    # end to end through the public API with host buffers: H2D of the initial fields,
+    # K steps, D2H of the final fields, all inside the timed region
+    host_in = {k: torch.from_numpy(v).pin_memory() for k, v in f32.items()}
+    host_out = [torch.empty((NY, NX), dtype=torch.float32).pin_memory() for _ in range(5)]
+    barrier()
+    t0 = time.perf_counter()
+    lat.init(**host_in)
+    lat.step(args.steps)
+    lat._check(lat.lib.tpflbm_get_fields(lat.h, *[__import__("ctypes").c_void_p(t.data_ptr()) for t in host_out]))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        return
+    units = NX * NY * args.steps * world
+    value = units / (total_ms * 1e-3) / 1e6
+    per_launch_s = total_ms * 1e-3 / args.steps
+    alg = ALG_BYTES[args.storage] * NX * NY
+    peak, peak_kind = _peaks()
+    achieved = alg / per_launch_s / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        mlups, steps, el, cores = run_oracle_sample(CPU_SAMPLE_SECONDS)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "%d FP64 oracle steps of the %dx%d bubble channel (%.1f s)" % (steps, NX, NY, el)}
+    field_bytes = 5 * 4 * NX * NY
+    line = {
+        "metric": "coupled-LBM MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "storage": args.storage,
+                   "l2": "256 MiB L2 flush between timed steps", "parallelism": "replicas"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": _traffic(args.storage),
+                     "peak_source": peak_kind, "alg_bytes_per_launch": alg,
+                     "kernel": "k_step"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": units / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": field_bytes / args.steps,
+                "d2h_bytes_per_step": field_bytes / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "check": {"nonfinite": diag["nonfinite"], "sum_phi": diag["sum_phi"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return bench_reference(args, rank, world)
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        bench_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * tpflbm — GB300 (sm_103a) library for the phase-field thermocapillary lattice
+ * Boltzmann method of Wang, He & Wang, "Phase-field-based lattice Boltzmann model
+ * for simulating thermocapillary flows" (arXiv 2306.11320).
+ *
+ * One lattice of nx x ny nodes (D2Q9, dx = dt = 1, Sec. 4) carries three sets of
+ * populations: f (conservative Allen-Cahn LBE, Eq. 14), g (pressure-based
+ * Navier-Stokes LBE, Sec. 3.1) and h (the heat-capacitance weighted thermal LBE,
+ * Eq. 28).  tpflbm_step advances all three by one time step per call of the
+ * fused step kernel: moments, isotropic stencils, closures (Eq. 45), interfacial
+ * force with the Marangoni stress (Eq. 11), BGK collisions, streaming and the
+ * wall / inlet / outflow rules of Sec. 4.
+ *
+ * Conventions for every call:
+ *   - Return value 0 (TPF_OK) on success, a negative TPF_ERR_* code otherwise; the
+ *     message of the last failure on a handle is tpflbm_last_error(handle).  No C++
+ *     exception crosses this interface.
+ *   - Fields are float32, row-major [ny][nx], y = 0 the bottom fluid row; walls sit
+ *     halfway, at y = -1/2 and y = ny - 1/2; the inlet at x = -1/2, the outflow
+ *     plane at x = nx - 1/2.  Populations are [9][ny][nx] per LBE in the D2Q9 order
+ *     of Eq. 43: rest, (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
+ *   - A field pointer may point to host memory or to device memory of the
+ *     handle's device; the library finds out which.  Caller-owned buffers stay
+ *     caller-owned; the library copies what it needs before returning.
+ *   - Work is ordered on the handle's CUDA stream (tpflbm_set_stream; default:
+ *     the legacy default stream).  Calls that return data to the caller
+ *     synchronise that stream before returning.
+ */
+#ifndef TPFLBM_H
+#define TPFLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPF_OK 0
+#define TPF_ERR_INVALID_ARG (-1)
+#define TPF_ERR_OOM (-2)
+#define TPF_ERR_CUDA (-3)
+#define TPF_ERR_NONFINITE (-4)
+#define TPF_ERR_TIMEOUT (-5)
+#define TPF_ERR_UNSUPPORTED (-6)
+
+#define TPF_STORAGE_FP32 0 /* populations stored as float32 */
+#define TPF_STORAGE_FP16 1 /* populations stored as scaled float16 deviations */
+
+typedef struct tpflbm *tpflbm_t;
+
+/* Physical parameters in lattice units (Sec. 2-4 of the paper).
+ *   rho, mu, lambda, cp (_l light phase phi = -1, _h heavy phase phi = +1):
+ *       interpolated linearly in phi, Eq. 45 (rho also Eq. 8); tau_g from
+ *       mu = rho cs2 (tau_g - 1/2), tau_h from lambda = cs2 (tau_h - 1/2).
+ *   W, M_phi: interface width and mobility, M_phi = cs2 (tau_phi - 1/2) (Sec. 3.1).
+ *   sigma_law 0: sigma = sigma_ref + sigma_T (T - T_ref) (Eq. 12);
+ *   sigma_law 1: sigma = sigma_TT (T - T_ref)^2 / 2 + sigma_ref (Eq. 63).
+ *   Gx, Gy: body-force density G of Eq. 7.
+ *   bc_x 0: periodic in x; 1: velocity inlet u_x(y) = 6 u_ave y (H - y) / H^2 with
+ *       phi = phi_in and T = T_in at x = -1/2, stress-free outflow (p = p_out,
+ *       zero-gradient phi and T) at x = nx - 1/2 (Sec. 4.3).
+ *   bc_y 0: halfway no-slip walls with Dirichlet temperature
+ *       T_bottom(x) = T_bot + T_bot_amp cos(2 pi T_bot_k x / nx) + T_bot_slope x,
+ *       T_top(x) = T_top + T_top_slope x (Sec. 4.1-4.3); 1: periodic in y.
+ *   storage: TPF_STORAGE_FP32 or TPF_STORAGE_FP16.  With FP16 the stored value of a
+ *       population q of LBE k is s_k (q - w_i X_k) in float16, with the power-of-two
+ *       scales fp16_scale_f/g/h (0 selects a default) and X_h = fp16_ref_T
+ *       (X_f = X_g = 0); arithmetic stays float32.
+ */
+typedef struct tpflbm_params {
+    double rho_l, rho_h, mu_l, mu_h, lambda_l, lambda_h, cp_l, cp_h;
+    double W, M_phi;
+    double sigma_ref, sigma_T, sigma_TT, T_ref;
+    double Gx, Gy;
+    double u_ave, phi_in, T_in, p_out;
+    double T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
+    double fp16_scale_f, fp16_scale_g, fp16_scale_h, fp16_ref_T;
+    int sigma_law, bc_x, bc_y, storage;
+} tpflbm_params;
+
+/* Device bytes tpflbm_create_in needs for an nx x ny lattice with these
+ * parameters (both population buffers, (phi u) of the previous step, field and
+ * reduction scratch).  Returns 0 for invalid sizes. */
+size_t tpflbm_workspace_bytes(int nx, int ny, const tpflbm_params *p);
+
+/* Create a lattice; the library allocates its device memory (cudaMalloc) on the
+ * current device and frees it in tpflbm_destroy.  nx, ny >= 3; relaxation times
+ * must exceed 1/2.  *out receives the handle. */
+int tpflbm_create(int nx, int ny, const tpflbm_params *p, tpflbm_t *out);
+
+/* Same, in caller-owned device memory `workspace` of at least
+ * tpflbm_workspace_bytes(nx, ny, p) bytes, 256-byte aligned, on the current
+ * device; the caller keeps it alive until tpflbm_destroy and frees it after. */
+int tpflbm_create_in(int nx, int ny, const tpflbm_params *p, void *workspace, size_t bytes,
+                     tpflbm_t *out);
+
+/* Order all later work of the handle on `stream` (a cudaStream_t; NULL = legacy
+ * default stream). */
+int tpflbm_set_stream(tpflbm_t h, void *stream);
+
+/* Initial populations from macroscopic fields (the paper gives none):
+ * f = f^eq(phi, u), g = g^eq(p, rho(phi), u), h = w_i T (Sec. 3), and the previous
+ * (phi u) = phi u.  Each pointer is a [ny][nx] float32 field; NULL means zero
+ * (for phi: +1).  Resets the step counter. */
+int tpflbm_init(tpflbm_t h, const float *phi, const float *ux, const float *uy, const float *p,
+                const float *T);
+
+/* Advance nsteps >= 0 time steps (one fused step-kernel launch each), enqueued
+ * on the handle's stream; returns after enqueueing. */
+int tpflbm_step(tpflbm_t h, long long nsteps);
+
+/* Macroscopic fields of the current state, as the next step computes them:
+ * phi = sum f_i, T = sum h_i, u from rho u = sum c_i g_i + (Fs + G)/2 and p from the
+ * pressure moment of Sec. 3.1.  Each output is a caller-owned [ny][nx] float32
+ * buffer (host or device) or NULL to skip.  Synchronises the stream. */
+int tpflbm_get_fields(tpflbm_t h, float *phi, float *ux, float *uy, float *p, float *T);
+
+/* Raw state as float32: f, g, h each [9][ny][nx] (decoded from FP16 storage when
+ * used), phiu [2][ny][nx] = (phi u) of the previous step.  NULL skips an array.
+ * Synchronises the stream. */
+int tpflbm_get_state(tpflbm_t h, float *f, float *g, float *hh, float *phiu);
+
+/* Overwrite the state (same layouts; encoded to FP16 when that storage is used).
+ * All four pointers are required. */
+int tpflbm_set_state(tpflbm_t h, const float *f, const float *g, const float *hh, const float *phiu);
+
+/* FP64 reductions of the current state (accumulated in double on the device):
+ * out[0] sum phi, out[1] sum rho c_p T, out[2] sum T, out[3] U_r numerator
+ * sum_{phi<0} phi u_y, out[4] U_r denominator sum_{phi<0} phi, out[5] sum_{phi<0} phi u_x,
+ * out[6] sum_{phi<0} phi x, out[7] number of non-finite phi, u or T values.
+ * U_r = out[3] / out[4] is the migration velocity of Sec. 4.2.  Synchronises. */
+int tpflbm_diagnostics(tpflbm_t h, double out[8]);
+
+/* Number of time steps taken since tpflbm_init. */
+long long tpflbm_time(tpflbm_t h);
+
+/* Release the handle and the device memory the library allocated.  NULL-safe. */
+void tpflbm_destroy(tpflbm_t h);
+
+/* Message of the last failure on h (or of the last failed create when h is NULL). */
+const char *tpflbm_last_error(tpflbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPFLBM_H */
