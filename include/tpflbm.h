@@ -62,10 +62,12 @@ typedef struct tpflbm *tpflbm_t;
  *   bc_y 0: halfway no-slip walls with Dirichlet temperature
  *       T_bottom(x) = T_bot + T_bot_amp cos(2 pi T_bot_k x / nx) + T_bot_slope x,
  *       T_top(x) = T_top + T_top_slope x (Sec. 4.1-4.3); 1: periodic in y.
- *   storage: TPF_STORAGE_FP32 or TPF_STORAGE_FP16.  With FP16 the stored value of a
- *       population q of LBE k is s_k (q - w_i X_k) in float16, with the power-of-two
- *       scales fp16_scale_f/g/h (0 selects a default) and X_h = fp16_ref_T
- *       (X_f = X_g = 0); arithmetic stays float32.
+ *   storage: TPF_STORAGE_FP32 or TPF_STORAGE_FP16.  With FP16 a population q_i of
+ *       LBE k is stored in float16 as s_k (q_i - r_i), its deviation from the rest
+ *       equilibrium of its node at the previous time level: r_i = w_i phi for f,
+ *       w_i T for h, 0 for g (phi and T of every node are kept in float32 for this).
+ *       s_k are powers of two, fp16_scale_f/g/h (0 selects the defaults 1024, 1024,
+ *       64).  All arithmetic stays float32.
  */
 typedef struct tpflbm_params {
     double rho_l, rho_h, mu_l, mu_h, lambda_l, lambda_h, cp_l, cp_h;
@@ -74,7 +76,7 @@ typedef struct tpflbm_params {
     double Gx, Gy;
     double u_ave, phi_in, T_in, p_out;
     double T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
-    double fp16_scale_f, fp16_scale_g, fp16_scale_h, fp16_ref_T;
+    double fp16_scale_f, fp16_scale_g, fp16_scale_h;
     int sigma_law, bc_x, bc_y, storage;
 } tpflbm_params;
 

@@ -16,7 +16,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpflbm_oracle.c")
-_LIB = os.path.join(_HERE, "_build", "libtpflbm_oracle.so")
+_LIBS = {"double": os.path.join(_HERE, "_build", "libtpflbm_oracle.so"),
+         "float": os.path.join(_HERE, "_build", "libtpflbm_oracle_f32.so")}
+_LIB = _LIBS["double"]
 
 _PARAM_DOUBLES = [
     "rho_l", "rho_h", "mu_l", "mu_h", "lambda_l", "lambda_h", "cp_l", "cp_h",
@@ -33,19 +35,55 @@ class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in _PARAM_DOUBLES] + [(n, C.c_int) for n in _PARAM_INTS]
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP over rows) into oracle/_build."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + ".%d.tmp" % os.getpid()
+def build_oracle(force: bool = False, real: str = "double") -> str:
+    """Compile the oracle with gcc (OpenMP over rows) into oracle/_build.
+
+    real="double" is the reference.  real="float" builds the same source in float32
+    arithmetic; it only serves to measure the float32 rounding floor of the method."""
+    lib = _LIBS[real]
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(_SRC):
+        return lib
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    if real == "float":
+        cmd[1:1] = ["-DORACLE_REAL=float", "-fsingle-precision-constant"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 _lib = None
+_lib32 = None
+
+
+def _sim_signatures(lib):
+    dp = C.POINTER(C.c_double)
+    vp = C.c_void_p
+    lib.orc_create.argtypes = [C.c_int, C.c_int, C.POINTER(OrcParams), C.POINTER(vp)]
+    lib.orc_create.restype = C.c_int
+    lib.orc_destroy.argtypes = [vp]
+    lib.orc_init.argtypes = [vp, dp, dp, dp, dp, dp]
+    lib.orc_init.restype = C.c_int
+    lib.orc_step.argtypes = [vp, C.c_longlong]
+    lib.orc_step.restype = C.c_int
+    lib.orc_get_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+    lib.orc_get_state.argtypes = [vp, dp, dp, dp, dp]
+    lib.orc_set_state.argtypes = [vp, dp, dp, dp, dp]
+    lib.orc_get_aux.argtypes = [vp, dp]
+    lib.orc_time.argtypes = [vp]
+    lib.orc_time.restype = C.c_longlong
+    lib.orc_num_threads.restype = C.c_int
+    lib.orc_set_num_threads.argtypes = [C.c_int]
+
+
+def _load32():
+    global _lib32
+    if _lib32 is None:
+        lib = C.CDLL(build_oracle(real="float"))
+        _sim_signatures(lib)
+        _lib32 = lib
+    return _lib32
 
 
 def _load():
@@ -53,22 +91,7 @@ def _load():
     if _lib is None:
         lib = C.CDLL(build_oracle())
         dp = C.POINTER(C.c_double)
-        vp = C.c_void_p
-        lib.orc_create.argtypes = [C.c_int, C.c_int, C.POINTER(OrcParams), C.POINTER(vp)]
-        lib.orc_create.restype = C.c_int
-        lib.orc_destroy.argtypes = [vp]
-        lib.orc_init.argtypes = [vp, dp, dp, dp, dp, dp]
-        lib.orc_init.restype = C.c_int
-        lib.orc_step.argtypes = [vp, C.c_longlong]
-        lib.orc_step.restype = C.c_int
-        lib.orc_get_fields.argtypes = [vp, dp, dp, dp, dp, dp]
-        lib.orc_get_state.argtypes = [vp, dp, dp, dp, dp]
-        lib.orc_set_state.argtypes = [vp, dp, dp, dp, dp]
-        lib.orc_get_aux.argtypes = [vp, dp]
-        lib.orc_time.argtypes = [vp]
-        lib.orc_time.restype = C.c_longlong
-        lib.orc_num_threads.restype = C.c_int
-        lib.orc_set_num_threads.argtypes = [C.c_int]
+        _sim_signatures(lib)
         lib.orc_feq.argtypes = [C.c_double] * 3 + [dp]
         lib.orc_Ri.argtypes = [C.c_double] * 6 + [dp]
         lib.orc_geq.argtypes = [C.c_double] * 4 + [dp]
@@ -168,13 +191,14 @@ class node_ops:
 
 
 class OracleSim:
-    """One lattice of nx x ny nodes advanced by the FP64 oracle.
+    """One lattice of nx x ny nodes advanced by the FP64 oracle (real="float": the
+    same algorithm in float32, for the rounding-floor measurement only).
 
     Fields are numpy arrays of shape (ny, nx), row-major, y = 0 the bottom row.
     """
 
-    def __init__(self, nx: int, ny: int, params: dict):
-        self.lib = _load()
+    def __init__(self, nx: int, ny: int, params: dict, real: str = "double"):
+        self.lib = _load() if real == "double" else _load32()
         self.nx, self.ny = int(nx), int(ny)
         self._p = _params(params)
         h = C.c_void_p()

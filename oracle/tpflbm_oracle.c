@@ -42,7 +42,7 @@
  *       (the h copy is the adiabatic condition).
  *   R10 (phi u) at the step before the first is phi0 u0 of the initial fields.
  */
-#include <math.h>
+#include <tgmath.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -52,15 +52,23 @@
 
 #define Q 9
 
+/* Arithmetic type of the oracle: double (the reference).  A float build
+ * (-DORACLE_REAL=float -fsingle-precision-constant) evaluates the same algorithm in
+ * float32; tests use it only to measure the float32 rounding floor of the method. */
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+
 /* D2Q9 velocity set in the paper's order (Sec. 4, Eq. 43): rest, the four axis
  * directions at angles (i-1) pi/2, the four diagonals at angles (2i-1) pi/4. */
 static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static const double WQ[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+static const real WQ[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-static const double CS2 = 1.0 / 3.0;
+static const real CS2 = 1.0 / 3.0;
 /* order-parameter values of the two bulk phases (Sec. 2) */
-static const double PHI_L = -1.0, PHI_H = 1.0;
+static const real PHI_L = -1.0, PHI_H = 1.0;
 
 typedef struct {
     double rho_l, rho_h, mu_l, mu_h, lambda_l, lambda_h, cp_l, cp_h;
@@ -75,17 +83,29 @@ typedef struct {
     int pad_;
 } orc_params;
 
+/* the parameters in the oracle's arithmetic type */
+typedef struct {
+    real rho_l, rho_h, mu_l, mu_h, lambda_l, lambda_h, cp_l, cp_h;
+    real W, M_phi;
+    real sigma_ref, sigma_T, sigma_TT, T_ref;
+    real Gx, Gy;
+    real u_ave, phi_in, T_in, p_out;
+    real T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
+    int sigma_law, bc_x, bc_y;
+} rparams;
+
 typedef struct {
     orc_params P;
+    rparams R;
     int nx, ny;
     long long t;
-    double *f, *g, *h;          /* [Q][ny][nx] pre-collision populations at time t */
-    double *fs, *gs, *hs;       /* post-collision scratch */
-    double *f2, *g2, *h2;       /* next-time buffers */
-    double *phiu_prev;          /* [2][ny][nx]: (phi u) at the previous step */
+    real *f, *g, *h;          /* [Q][ny][nx] pre-collision populations at time t */
+    real *fs, *gs, *hs;       /* post-collision scratch */
+    real *f2, *g2, *h2;       /* next-time buffers */
+    real *phiu_prev;          /* [2][ny][nx]: (phi u) at the previous step */
     /* macroscopic fields of the current time level */
-    double *phi, *T, *ux, *uy, *p, *rho, *rcp, *tau_g, *tau_h, *Fhat;
-    double *dphiux, *dphiuy, *nx_, *ny_, *Fx, *Fy, *gradrx, *gradry;
+    real *phi, *T, *ux, *uy, *p, *rho, *rcp, *tau_g, *tau_h, *Fhat;
+    real *dphiux, *dphiuy, *nx_, *ny_, *Fx, *Fy, *gradrx, *gradry;
 } orc_sim;
 
 /* ---------------------------------------------------------------- lattice */
@@ -112,78 +132,78 @@ static int opposite(int i)
 /* ------------------------------------------------------ per-node operators */
 
 /* Property interpolation, Eq. 45: linear in phi between the two bulk values. */
-double orc_interp(double phi, double xi_l, double xi_h)
+real orc_interp(real phi, real xi_l, real xi_h)
 {
-    double pc = phi < PHI_L ? PHI_L : (phi > PHI_H ? PHI_H : phi); /* R6 */
+    real pc = phi < PHI_L ? PHI_L : (phi > PHI_H ? PHI_H : phi); /* R6 */
     return (pc - PHI_H) / (PHI_L - PHI_H) * xi_l + (pc - PHI_L) / (PHI_H - PHI_L) * xi_h;
 }
 
 /* Allen-Cahn equilibrium, Sec. 3.1: f_i^eq = w_i phi (1 + c_i.u / cs2). */
-void orc_feq(double phi, double ux, double uy, double *out)
+void orc_feq(real phi, real ux, real uy, real *out)
 {
     for (int i = 0; i < Q; ++i) {
-        double cu = EX[i] * ux + EY[i] * uy;
+        real cu = EX[i] * ux + EY[i] * uy;
         out[i] = WQ[i] * phi * (1.0 + cu / CS2);
     }
 }
 
 /* Allen-Cahn source, Sec. 3.1:
  * R_i = w_i c_i.[ d_t(phi u) + cs2 n (1 - phi^2) / (sqrt2 W) ] / cs2. */
-void orc_Ri(double phi, double dphiux, double dphiuy, double nx, double ny, double W,
-            double *out)
+void orc_Ri(real phi, real dphiux, real dphiuy, real nx, real ny, real W,
+            real *out)
 {
-    double theta = (1.0 - phi * phi) / (sqrt(2.0) * W);
-    double ax = dphiux + CS2 * nx * theta;
-    double ay = dphiuy + CS2 * ny * theta;
+    real theta = (1.0 - phi * phi) / (sqrt(2.0) * W);
+    real ax = dphiux + CS2 * nx * theta;
+    real ay = dphiuy + CS2 * ny * theta;
     for (int i = 0; i < Q; ++i) out[i] = WQ[i] * (EX[i] * ax + EY[i] * ay) / CS2;
 }
 
 /* s_i(u) of the NS equilibrium, Sec. 3.1. */
-static double s_i(int i, double ux, double uy)
+static real s_i(int i, real ux, real uy)
 {
-    double cu = EX[i] * ux + EY[i] * uy;
-    double uu = ux * ux + uy * uy;
+    real cu = EX[i] * ux + EY[i] * uy;
+    real uu = ux * ux + uy * uy;
     return WQ[i] * (cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
 }
 
 /* Pressure-based NS equilibrium, Sec. 3.1:
  * g_0^eq = p/cs2 (w_0 - 1) + rho s_0(u),  g_i^eq = p/cs2 w_i + rho s_i(u). */
-void orc_geq(double p, double rho, double ux, double uy, double *out)
+void orc_geq(real p, real rho, real ux, real uy, real *out)
 {
     for (int i = 0; i < Q; ++i) {
-        double wp = (i == 0) ? (WQ[0] - 1.0) : WQ[i];
+        real wp = (i == 0) ? (WQ[0] - 1.0) : WQ[i];
         out[i] = p / CS2 * wp + rho * s_i(i, ux, uy);
     }
 }
 
 /* NS forcing, Sec. 3.1:
  * G_i = w_i [ u.grad rho + c_i.(Fs + G)/cs2 + u grad rho : (c_i c_i - cs2 I)/cs2 ]. */
-void orc_Gi(double ux, double uy, double grx, double gry, double Fx, double Fy, double *out)
+void orc_Gi(real ux, real uy, real grx, real gry, real Fx, real Fy, real *out)
 {
-    double ug = ux * grx + uy * gry;
+    real ug = ux * grx + uy * gry;
     for (int i = 0; i < Q; ++i) {
-        double cF = EX[i] * Fx + EY[i] * Fy;
-        double cu = EX[i] * ux + EY[i] * uy;
-        double cg = EX[i] * grx + EY[i] * gry;
-        double dyad = cu * cg - CS2 * ug; /* u grad rho : (c c - cs2 I) */
+        real cF = EX[i] * Fx + EY[i] * Fy;
+        real cu = EX[i] * ux + EY[i] * uy;
+        real cg = EX[i] * grx + EY[i] * gry;
+        real dyad = cu * cg - CS2 * ug; /* u grad rho : (c c - cs2 I) */
         out[i] = WQ[i] * (ug + cF / CS2 + dyad / CS2);
     }
 }
 
 /* Thermal equilibrium, Eq. 31 (labelled weq_31): h_i^eq = w_i T. */
-void orc_heq(double T, double *out)
+void orc_heq(real T, real *out)
 {
     for (int i = 0; i < Q; ++i) out[i] = WQ[i] * T;
 }
 
 /* Thermal source, Eq. 30: Fhat_i = w_i Fhat. */
-void orc_Fhat_i(double Fhat, double *out)
+void orc_Fhat_i(real Fhat, real *out)
 {
     for (int i = 0; i < Q; ++i) out[i] = WQ[i] * Fhat;
 }
 
 /* Surface tension law: linear (Eq. 12) or parabolic (Eq. 63), and dsigma/dT. */
-static void sigma_of_T(const orc_params *P, double T, double *sig, double *dsig)
+static void sigma_of_T(const rparams *P, real T, real *sig, real *dsig)
 {
     if (P->sigma_law == 1) {
         *sig = 0.5 * P->sigma_TT * (T - P->T_ref) * (T - P->T_ref) + P->sigma_ref;
@@ -197,41 +217,41 @@ static void sigma_of_T(const orc_params *P, double T, double *sig, double *dsig)
 /* Interfacial force, last line of Eq. 11:
  * Fs = 3 sqrt2 W / 4 [ |grad phi|^2 grad sigma - (grad sigma . grad phi) grad phi
  *                      + sigma mu_phi grad phi / W^2 ]. */
-void orc_Fs(double W, double sigma, double gsx, double gsy, double mu_phi, double gpx,
-            double gpy, double *Fx, double *Fy)
+void orc_Fs(real W, real sigma, real gsx, real gsy, real mu_phi, real gpx,
+            real gpy, real *Fx, real *Fy)
 {
-    double k = 3.0 * sqrt(2.0) * W / 4.0;
-    double g2 = gpx * gpx + gpy * gpy;
-    double sp = gsx * gpx + gsy * gpy;
+    real k = 3.0 * sqrt(2.0) * W / 4.0;
+    real g2 = gpx * gpx + gpy * gpy;
+    real sp = gsx * gpx + gsy * gpy;
     *Fx = k * (g2 * gsx - sp * gpx + sigma * mu_phi * gpx / (W * W));
     *Fy = k * (g2 * gsy - sp * gpy + sigma * mu_phi * gpy / (W * W));
 }
 
 /* Chemical potential (Sec. 2, after Eq. 11):
  * mu_phi = (phi - phi_l)(phi - phi_h)(phi - (phi_l + phi_h)/2) - W^2 lap phi. */
-double orc_mu_phi(double phi, double lap, double W)
+real orc_mu_phi(real phi, real lap, real W)
 {
     return (phi - PHI_L) * (phi - PHI_H) * (phi - 0.5 * (PHI_L + PHI_H)) - W * W * lap;
 }
 
 /* ------------------------------------------------------------ wall values */
 
-static double T_wall_bottom(const orc_params *P, int nx, double x)
+static real T_wall_bottom(const rparams *P, int nx, real x)
 {
-    const double pi = 3.14159265358979323846;
+    const real pi = 3.14159265358979323846;
     return P->T_bot + P->T_bot_amp * cos(2.0 * pi * P->T_bot_k * x / nx) + P->T_bot_slope * x;
 }
 
-static double T_wall_top(const orc_params *P, double x)
+static real T_wall_top(const rparams *P, real x)
 {
     return P->T_top + P->T_top_slope * x;
 }
 
 /* Poiseuille inlet profile along x (Sec. 4.3, Eq. 62 with u along the channel):
  * y is measured from the bottom wall, H = ny. */
-static double u_inlet(const orc_params *P, int ny, double y)
+static real u_inlet(const rparams *P, int ny, real y)
 {
-    double H = (double)ny;
+    real H = (real)ny;
     return 6.0 * P->u_ave * y * (H - y) / (H * H);
 }
 
@@ -240,34 +260,34 @@ static double u_inlet(const orc_params *P, int ny, double y)
 static inline size_t IDX(const orc_sim *s, int x, int y) { return (size_t)y * s->nx + x; }
 
 /* phi at a lattice point one step outside the fluid (R3). */
-static double phi_at(const orc_sim *s, int x, int y)
+static real phi_at(const orc_sim *s, int x, int y)
 {
     if (y < 0 || y >= s->ny) {
-        if (s->P.bc_y == 1) y = (y + s->ny) % s->ny;
+        if (s->R.bc_y == 1) y = (y + s->ny) % s->ny;
         else y = y < 0 ? 0 : s->ny - 1;
     }
     if (x < 0 || x >= s->nx) {
-        if (s->P.bc_x == 0) x = (x + s->nx) % s->nx;
+        if (s->R.bc_x == 0) x = (x + s->nx) % s->nx;
         else x = x < 0 ? 0 : s->nx - 1;
     }
     return s->phi[IDX(s, x, y)];
 }
 
 /* T at a lattice point one step outside the fluid (R3). */
-static double T_at(const orc_sim *s, int x, int y)
+static real T_at(const orc_sim *s, int x, int y)
 {
     if (y < 0 || y >= s->ny) {
-        if (s->P.bc_y == 1) {
+        if (s->R.bc_y == 1) {
             y = (y + s->ny) % s->ny;
         } else if (y < 0) {
-            return 2.0 * T_wall_bottom(&s->P, s->nx, (double)x) - T_at(s, x, 0);
+            return 2.0 * T_wall_bottom(&s->R, s->nx, (real)x) - T_at(s, x, 0);
         } else {
-            return 2.0 * T_wall_top(&s->P, (double)x) - T_at(s, x, s->ny - 1);
+            return 2.0 * T_wall_top(&s->R, (real)x) - T_at(s, x, s->ny - 1);
         }
     }
     if (x < 0 || x >= s->nx) {
-        if (s->P.bc_x == 0) x = (x + s->nx) % s->nx;
-        else if (x < 0) return 2.0 * s->P.T_in - s->T[IDX(s, 0, y)];
+        if (s->R.bc_x == 0) x = (x + s->nx) % s->nx;
+        else if (x < 0) return 2.0 * s->R.T_in - s->T[IDX(s, 0, y)];
         else return s->T[IDX(s, s->nx - 1, y)];
     }
     return s->T[IDX(s, x, y)];
@@ -275,7 +295,40 @@ static double T_at(const orc_sim *s, int x, int y)
 
 /* ------------------------------------------------------------ life cycle */
 
-static double *alloc0(size_t n) { return (double *)calloc(n, sizeof(double)); }
+static void real_params(const orc_params *P, rparams *R)
+{
+    R->rho_l = (real)P->rho_l;
+    R->rho_h = (real)P->rho_h;
+    R->mu_l = (real)P->mu_l;
+    R->mu_h = (real)P->mu_h;
+    R->lambda_l = (real)P->lambda_l;
+    R->lambda_h = (real)P->lambda_h;
+    R->cp_l = (real)P->cp_l;
+    R->cp_h = (real)P->cp_h;
+    R->W = (real)P->W;
+    R->M_phi = (real)P->M_phi;
+    R->sigma_ref = (real)P->sigma_ref;
+    R->sigma_T = (real)P->sigma_T;
+    R->sigma_TT = (real)P->sigma_TT;
+    R->T_ref = (real)P->T_ref;
+    R->Gx = (real)P->Gx;
+    R->Gy = (real)P->Gy;
+    R->u_ave = (real)P->u_ave;
+    R->phi_in = (real)P->phi_in;
+    R->T_in = (real)P->T_in;
+    R->p_out = (real)P->p_out;
+    R->T_bot = (real)P->T_bot;
+    R->T_bot_amp = (real)P->T_bot_amp;
+    R->T_bot_k = (real)P->T_bot_k;
+    R->T_bot_slope = (real)P->T_bot_slope;
+    R->T_top = (real)P->T_top;
+    R->T_top_slope = (real)P->T_top_slope;
+    R->sigma_law = P->sigma_law;
+    R->bc_x = P->bc_x;
+    R->bc_y = P->bc_y;
+}
+
+static real *alloc0(size_t n) { return (real *)calloc(n, sizeof(real)); }
 
 int orc_create(int nx, int ny, const orc_params *P, orc_sim **out)
 {
@@ -283,6 +336,7 @@ int orc_create(int nx, int ny, const orc_params *P, orc_sim **out)
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return -2;
     s->P = *P;
+    real_params(P, &s->R);
     s->nx = nx;
     s->ny = ny;
     size_t N = (size_t)nx * ny;
@@ -303,7 +357,7 @@ int orc_create(int nx, int ny, const orc_params *P, orc_sim **out)
 void orc_destroy(orc_sim *s)
 {
     if (!s) return;
-    double *bufs[] = {s->f, s->g, s->h, s->fs, s->gs, s->hs, s->f2, s->g2, s->h2,
+    real *bufs[] = {s->f, s->g, s->h, s->fs, s->gs, s->hs, s->f2, s->g2, s->h2,
                       s->phiu_prev, s->phi, s->T, s->ux, s->uy, s->p, s->rho, s->rcp,
                       s->tau_g, s->tau_h, s->Fhat, s->dphiux, s->dphiuy, s->nx_, s->ny_,
                       s->Fx, s->Fy, s->gradrx, s->gradry};
@@ -317,40 +371,50 @@ int orc_init(orc_sim *s, const double *phi, const double *ux, const double *uy,
              const double *p, const double *T)
 {
     size_t N = (size_t)s->nx * s->ny;
-    double e[Q];
+    real e[Q];
     for (size_t n = 0; n < N; ++n) {
-        double rho = orc_interp(phi[n], s->P.rho_l, s->P.rho_h);
-        orc_feq(phi[n], ux[n], uy[n], e);
+        real rho = orc_interp((real)phi[n], s->R.rho_l, s->R.rho_h);
+        orc_feq((real)phi[n], (real)ux[n], (real)uy[n], e);
         for (int i = 0; i < Q; ++i) s->f[i * N + n] = e[i];
-        orc_geq(p[n], rho, ux[n], uy[n], e);
+        orc_geq((real)p[n], rho, (real)ux[n], (real)uy[n], e);
         for (int i = 0; i < Q; ++i) s->g[i * N + n] = e[i];
-        orc_heq(T[n], e);
+        orc_heq((real)T[n], e);
         for (int i = 0; i < Q; ++i) s->h[i * N + n] = e[i];
-        s->phiu_prev[n] = phi[n] * ux[n];
-        s->phiu_prev[N + n] = phi[n] * uy[n];
+        s->phiu_prev[n] = (real)phi[n] * (real)ux[n];
+        s->phiu_prev[N + n] = (real)phi[n] * (real)uy[n];
     }
     s->t = 0;
     return 0;
+}
+
+static void to_real(real *dst, const double *src, size_t n)
+{
+    for (size_t k = 0; k < n; ++k) dst[k] = (real)src[k];
+}
+
+static void to_double(double *dst, const real *src, size_t n)
+{
+    for (size_t k = 0; k < n; ++k) dst[k] = (double)src[k];
 }
 
 int orc_set_state(orc_sim *s, const double *f, const double *g, const double *h,
                   const double *phiu_prev)
 {
     size_t N = (size_t)s->nx * s->ny;
-    memcpy(s->f, f, Q * N * sizeof(double));
-    memcpy(s->g, g, Q * N * sizeof(double));
-    memcpy(s->h, h, Q * N * sizeof(double));
-    memcpy(s->phiu_prev, phiu_prev, 2 * N * sizeof(double));
+    to_real(s->f, f, Q * N);
+    to_real(s->g, g, Q * N);
+    to_real(s->h, h, Q * N);
+    to_real(s->phiu_prev, phiu_prev, 2 * N);
     return 0;
 }
 
 int orc_get_state(const orc_sim *s, double *f, double *g, double *h, double *phiu_prev)
 {
     size_t N = (size_t)s->nx * s->ny;
-    if (f) memcpy(f, s->f, Q * N * sizeof(double));
-    if (g) memcpy(g, s->g, Q * N * sizeof(double));
-    if (h) memcpy(h, s->h, Q * N * sizeof(double));
-    if (phiu_prev) memcpy(phiu_prev, s->phiu_prev, 2 * N * sizeof(double));
+    if (f) to_double(f, s->f, Q * N);
+    if (g) to_double(g, s->g, Q * N);
+    if (h) to_double(h, s->h, Q * N);
+    if (phiu_prev) to_double(phiu_prev, s->phiu_prev, 2 * N);
     return 0;
 }
 
@@ -358,10 +422,10 @@ int orc_get_state(const orc_sim *s, double *f, double *g, double *h, double *phi
 
 static void macroscopic(orc_sim *s)
 {
-    const orc_params *P = &s->P;
+    const rparams *P = &s->R;
     const int nx = s->nx, ny = s->ny;
     const size_t N = (size_t)nx * ny;
-    const double tau_phi = P->M_phi / CS2 + 0.5; /* M_phi = cs2 (tau_phi - 1/2), Sec. 3.1 */
+    const real tau_phi = P->M_phi / CS2 + 0.5; /* M_phi = cs2 (tau_phi - 1/2), Sec. 3.1 */
     (void)tau_phi;
 
     /* pass 1: zeroth moments */
@@ -369,7 +433,7 @@ static void macroscopic(orc_sim *s)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = IDX(s, x, y);
-            double sf = 0.0, sh = 0.0;
+            real sf = 0.0, sh = 0.0;
             for (int i = 0; i < Q; ++i) {
                 sf += s->f[i * N + n];
                 sh += s->h[i * N + n];
@@ -383,13 +447,13 @@ static void macroscopic(orc_sim *s)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = IDX(s, x, y);
-            double phi = s->phi[n], T = s->T[n];
+            real phi = s->phi[n], T = s->T[n];
 
             /* isotropic stencils (R2) */
-            double gpx = 0, gpy = 0, lap = 0, gtx = 0, gty = 0;
+            real gpx = 0, gpy = 0, lap = 0, gtx = 0, gty = 0;
             for (int i = 1; i < Q; ++i) {
-                double pn = phi_at(s, x + EX[i], y + EY[i]);
-                double tn = T_at(s, x + EX[i], y + EY[i]);
+                real pn = phi_at(s, x + EX[i], y + EY[i]);
+                real tn = T_at(s, x + EX[i], y + EY[i]);
                 gpx += WQ[i] * EX[i] * pn;
                 gpy += WQ[i] * EY[i] * pn;
                 lap += 2.0 * WQ[i] * (pn - phi);
@@ -399,62 +463,62 @@ static void macroscopic(orc_sim *s)
             gpx /= CS2; gpy /= CS2; lap /= CS2; gtx /= CS2; gty /= CS2;
 
             /* closures: Eq. 45 for rho, mu, lambda and rho c_p */
-            double rho = orc_interp(phi, P->rho_l, P->rho_h);
-            double mu = orc_interp(phi, P->mu_l, P->mu_h);
-            double lam = orc_interp(phi, P->lambda_l, P->lambda_h);
-            double rcp = orc_interp(phi, P->rho_l * P->cp_l, P->rho_h * P->cp_h);
-            double tau_g = mu / (rho * CS2) + 0.5;     /* mu = rho cs2 (tau_g - 1/2) */
-            double tau_h = lam / CS2 + 0.5;            /* lambda = (tau_h - 1/2) cs2 */
+            real rho = orc_interp(phi, P->rho_l, P->rho_h);
+            real mu = orc_interp(phi, P->mu_l, P->mu_h);
+            real lam = orc_interp(phi, P->lambda_l, P->lambda_h);
+            real rcp = orc_interp(phi, P->rho_l * P->cp_l, P->rho_h * P->cp_h);
+            real tau_g = mu / (rho * CS2) + 0.5;     /* mu = rho cs2 (tau_g - 1/2) */
+            real tau_h = lam / CS2 + 0.5;            /* lambda = (tau_h - 1/2) cs2 */
 
             /* chemical potential and interfacial force with Marangoni stress */
-            double sig, dsig;
+            real sig, dsig;
             sigma_of_T(P, T, &sig, &dsig);
-            double mu_phi = orc_mu_phi(phi, lap, P->W);
-            double Fsx, Fsy;
+            real mu_phi = orc_mu_phi(phi, lap, P->W);
+            real Fsx, Fsy;
             orc_Fs(P->W, sig, dsig * gtx, dsig * gty, mu_phi, gpx, gpy, &Fsx, &Fsy);
-            double Fx = Fsx + P->Gx, Fy = Fsy + P->Gy;
+            real Fx = Fsx + P->Gx, Fy = Fsy + P->Gy;
 
             /* velocity: rho u = sum c_i g_i + dt/2 (Fs + G) */
-            double mx = 0, my = 0, s_ne0 = 0;
+            real mx = 0, my = 0, s_ne0 = 0;
             for (int i = 0; i < Q; ++i) {
-                double gi = s->g[i * N + n];
+                real gi = s->g[i * N + n];
                 mx += EX[i] * gi;
                 my += EY[i] * gi;
                 if (i != 0) s_ne0 += gi;
             }
-            double ux = (mx + 0.5 * Fx) / rho;
-            double uy = (my + 0.5 * Fy) / rho;
+            real ux = (mx + 0.5 * Fx) / rho;
+            real uy = (my + 0.5 * Fy) / rho;
 
             /* grad rho from Eq. 8 */
-            double drdphi = (P->rho_l - P->rho_h) / (PHI_L - PHI_H);
-            double grx = drdphi * gpx, gry = drdphi * gpy;
+            real drdphi = (P->rho_l - P->rho_h) / (PHI_L - PHI_H);
+            real grx = drdphi * gpx, gry = drdphi * gpy;
 
             /* pressure: p = cs2/(1 - w0) [ sum_{i!=0} g_i + dt/2 u.grad rho + rho s_0(u) ] */
-            double p = CS2 / (1.0 - WQ[0]) * (s_ne0 + 0.5 * (ux * grx + uy * gry) +
+            real p = CS2 / (1.0 - WQ[0]) * (s_ne0 + 0.5 * (ux * grx + uy * gry) +
                                               rho * s_i(0, ux, uy));
 
             /* d_t(phi u), first-order Euler (Eq. 44) */
-            double dpx = phi * ux - s->phiu_prev[n];
-            double dpy = phi * uy - s->phiu_prev[N + n];
+            real dpx = phi * ux - s->phiu_prev[n];
+            real dpy = phi * uy - s->phiu_prev[N + n];
 
             /* unit normal (R7) */
-            double gn = sqrt(gpx * gpx + gpy * gpy);
-            double nnx = 0.0, nny = 0.0;
+            real gn = sqrt(gpx * gpx + gpy * gpy);
+            real nnx = 0.0, nny = 0.0;
             if (gn > 1e-10) {
                 nnx = gpx / gn;
                 nny = gpy / gn;
             }
 
             /* local temperature gradient from the non-equilibrium part of h (Eq. 40, R4) */
-            double qx = 0, qy = 0;
+            real qx = 0, qy = 0;
             for (int i = 0; i < Q; ++i) {
-                double neq = s->h[i * N + n] - WQ[i] * T;
+                real neq = s->h[i * N + n] - WQ[i] * T;
                 qx += EX[i] * neq;
                 qy += EY[i] * neq;
             }
-            double gTx = -qx / (tau_h * CS2);
-            double gTy = -qy / (tau_h * CS2);
-            double Fhat = -rcp * (ux * gTx + uy * gTy); /* Eq. 27 source */
+            real gTx = -qx / (tau_h * CS2);
+            real gTy = -qy / (tau_h * CS2);
+            real Fhat = -rcp * (ux * gTx + uy * gTy); /* Eq. 27 source */
 
             s->ux[n] = ux; s->uy[n] = uy; s->p[n] = p; s->rho[n] = rho; s->rcp[n] = rcp;
             s->tau_g[n] = tau_g; s->tau_h[n] = tau_h; s->Fhat[n] = Fhat;
@@ -467,41 +531,41 @@ static void macroscopic(orc_sim *s)
 
 static void collide(orc_sim *s)
 {
-    const orc_params *P = &s->P;
+    const rparams *P = &s->R;
     const int nx = s->nx, ny = s->ny;
     const size_t N = (size_t)nx * ny;
-    const double tau_phi = P->M_phi / CS2 + 0.5;
+    const real tau_phi = P->M_phi / CS2 + 0.5;
 
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = IDX(s, x, y);
-            double eq[Q], src[Q];
+            real eq[Q], src[Q];
 
             /* Allen-Cahn LBE, Eq. 14 */
             orc_feq(s->phi[n], s->ux[n], s->uy[n], eq);
             orc_Ri(s->phi[n], s->dphiux[n], s->dphiuy[n], s->nx_[n], s->ny_[n], P->W, src);
             for (int i = 0; i < Q; ++i) {
-                double fi = s->f[i * N + n];
+                real fi = s->f[i * N + n];
                 s->fs[i * N + n] = fi - (fi - eq[i]) / tau_phi + (1.0 - 0.5 / tau_phi) * src[i];
             }
 
             /* Navier-Stokes LBE, Sec. 3.1 */
-            double tg = s->tau_g[n];
+            real tg = s->tau_g[n];
             orc_geq(s->p[n], s->rho[n], s->ux[n], s->uy[n], eq);
             orc_Gi(s->ux[n], s->uy[n], s->gradrx[n], s->gradry[n], s->Fx[n], s->Fy[n], src);
             for (int i = 0; i < Q; ++i) {
-                double gi = s->g[i * N + n];
+                real gi = s->g[i * N + n];
                 s->gs[i * N + n] = gi - (gi - eq[i]) / tg + (1.0 - 0.5 / tg) * src[i];
             }
 
             /* thermal LBE, Eq. 28: collision part (the rho c_p weighting is applied
              * in the streaming pass) */
-            double th = s->tau_h[n];
+            real th = s->tau_h[n];
             orc_heq(s->T[n], eq);
             orc_Fhat_i(s->Fhat[n], src);
             for (int i = 0; i < Q; ++i) {
-                double hi = s->h[i * N + n];
+                real hi = s->h[i * N + n];
                 s->hs[i * N + n] = hi - (hi - eq[i]) / th + src[i];
             }
         }
@@ -513,7 +577,7 @@ static void collide(orc_sim *s)
  * h_i(y, t+1) = h_i(y, t) + [ hstar_i(y - c_i) - h_i(y, t) ] / (rho c_p)(y). */
 static void stream(orc_sim *s)
 {
-    const orc_params *P = &s->P;
+    const rparams *P = &s->R;
     const int nx = s->nx, ny = s->ny;
     const size_t N = (size_t)nx * ny;
 
@@ -521,12 +585,12 @@ static void stream(orc_sim *s)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t n = IDX(s, x, y);
-            double rcp = s->rcp[n];
+            real rcp = s->rcp[n];
             for (int i = 0; i < Q; ++i) {
                 int sx = x - EX[i], sy = y - EY[i];
                 int o = opposite(i);
-                double hold = s->h[i * N + n];
-                double fnew, gnew, hin;
+                real hold = s->h[i * N + n];
+                real fnew, gnew, hin;
                 int out_y = (sy < 0 || sy >= ny) && P->bc_y == 0;
                 if (P->bc_y == 1) sy = (sy + ny) % ny;
                 int out_x = (sx < 0 || sx >= nx) && P->bc_x == 1;
@@ -535,16 +599,16 @@ static void stream(orc_sim *s)
                 if (out_y) {
                     /* halfway bounce-back (R8); anti-bounce-back for h with the wall
                      * temperature at the wall-crossing point of the link */
-                    double xc = x - 0.5 * EX[i];
-                    double Tw = (y - EY[i] < 0) ? T_wall_bottom(P, nx, xc) : T_wall_top(P, xc);
+                    real xc = x - 0.5 * EX[i];
+                    real Tw = (y - EY[i] < 0) ? T_wall_bottom(P, nx, xc) : T_wall_top(P, xc);
                     fnew = s->fs[o * N + n];
                     gnew = s->gs[o * N + n];
                     hin = -s->hs[o * N + n] + 2.0 * WQ[i] * Tw;
                 } else if (out_x && sx < 0) {
                     /* velocity inlet (R9) */
-                    double ycr = y + 0.5 - 0.5 * EY[i];
-                    double uin = u_inlet(P, ny, ycr);
-                    double cu = EX[i] * uin;
+                    real ycr = y + 0.5 - 0.5 * EY[i];
+                    real uin = u_inlet(P, ny, ycr);
+                    real cu = EX[i] * uin;
                     fnew = s->fs[o * N + n] + 2.0 * WQ[i] * P->phi_in * cu / CS2;
                     gnew = s->gs[o * N + n] + 2.0 * WQ[i] * s->rho[n] * cu / CS2;
                     hin = -s->hs[o * N + n] + 2.0 * WQ[i] * P->T_in;
@@ -552,9 +616,9 @@ static void stream(orc_sim *s)
                     /* outflow (R9): pressure anti-bounce-back for g with p = p_out and the
                      * node's own velocity; zero-gradient post-collision f and h */
                     size_t m = IDX(s, nx - 1, sy);
-                    double ux = s->ux[n], uy = s->uy[n];
-                    double cu = EX[i] * ux + EY[i] * uy;
-                    double sym = P->p_out / CS2 + s->rho[n] * (cu * cu / (2.0 * CS2 * CS2) -
+                    real ux = s->ux[n], uy = s->uy[n];
+                    real cu = EX[i] * ux + EY[i] * uy;
+                    real sym = P->p_out / CS2 + s->rho[n] * (cu * cu / (2.0 * CS2 * CS2) -
                                                                (ux * ux + uy * uy) / (2.0 * CS2));
                     fnew = s->fs[i * N + m];
                     gnew = -s->gs[o * N + n] + 2.0 * WQ[i] * sym;
@@ -572,9 +636,9 @@ static void stream(orc_sim *s)
         }
 }
 
-static void swap_ptr(double **a, double **b)
+static void swap_ptr(real **a, real **b)
 {
-    double *t = *a;
+    real *t = *a;
     *a = *b;
     *b = t;
 }
@@ -607,12 +671,11 @@ int orc_get_fields(orc_sim *s, double *phi, double *ux, double *uy, double *p, d
 {
     macroscopic(s);
     size_t N = (size_t)s->nx * s->ny;
-    size_t b = N * sizeof(double);
-    if (phi) memcpy(phi, s->phi, b);
-    if (ux) memcpy(ux, s->ux, b);
-    if (uy) memcpy(uy, s->uy, b);
-    if (p) memcpy(p, s->p, b);
-    if (T) memcpy(T, s->T, b);
+    if (phi) to_double(phi, s->phi, N);
+    if (ux) to_double(ux, s->ux, N);
+    if (uy) to_double(uy, s->uy, N);
+    if (p) to_double(p, s->p, N);
+    if (T) to_double(T, s->T, N);
     return 0;
 }
 
@@ -622,14 +685,13 @@ int orc_get_aux(orc_sim *s, double *out)
 {
     macroscopic(s);
     size_t N = (size_t)s->nx * s->ny;
-    size_t b = N * sizeof(double);
-    memcpy(out + 0 * N, s->rho, b);
-    memcpy(out + 1 * N, s->rcp, b);
-    memcpy(out + 2 * N, s->Fhat, b);
-    memcpy(out + 3 * N, s->Fx, b);
-    memcpy(out + 4 * N, s->Fy, b);
-    memcpy(out + 5 * N, s->tau_g, b);
-    memcpy(out + 6 * N, s->tau_h, b);
+    to_double(out + 0 * N, s->rho, N);
+    to_double(out + 1 * N, s->rcp, N);
+    to_double(out + 2 * N, s->Fhat, N);
+    to_double(out + 3 * N, s->Fx, N);
+    to_double(out + 4 * N, s->Fy, N);
+    to_double(out + 5 * N, s->tau_g, N);
+    to_double(out + 6 * N, s->tau_h, N);
     return 0;
 }
 

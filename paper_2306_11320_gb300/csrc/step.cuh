@@ -1,0 +1,483 @@
+// The fused time step of the three coupled LBEs (arXiv 2306.11320, Sec. 3-4):
+// a general tile routine (every boundary rule, thread loads) and a persistent
+// kernel that stages interior tiles in shared memory with TMA, double buffered.
+#pragma once
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lattice.cuh"
+
+namespace tpf {
+
+// FP16 storage keeps the scaled deviation s_k (q_i - r_i) of each population from
+// the rest equilibrium of the node it streamed from: r_i = w_i phi(src) for f,
+// w_i T(src) for h, 0 for g, with src = y - c_i (wrapped when periodic) and src = y
+// itself when y - c_i lies outside the fluid (a population reflected at a wall, the
+// inlet or the outflow plane).  phi and T of every node at the previous time level
+// are kept in two float planes ("ref").  The writer of a population is its source
+// node, so it encodes with its own phi and T.
+template <class S>
+constexpr bool kRef = std::is_same<S, StoreF16>::value;
+
+// node whose rest equilibrium is the FP16 reference of population i at (x, y)
+__device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int i)
+{
+    int sx = x - cx(i), sy = y - cy(i);
+    if (P.bc_x == 0) sx = wrap(sx, P.nx);
+    if (P.bc_y == 1) sy = wrap(sy, P.ny);
+    if (sx < 0 || sx >= P.nx || sy < 0 || sy >= P.ny) {
+        sx = x;
+        sy = y;
+    }
+    return sy * P.nx + sx;
+}
+
+// Decoded populations of node (x, y) read from global memory (general path).
+template <class S, bool WANT_G = true>
+__device__ __forceinline__ void load_node(const DevParams& P, const typename S::elem* __restrict__ A,
+                                          const float* __restrict__ ref, int x, int y, float* f, float* g,
+                                          float* h)
+{
+    const long long pl = P.plane;
+    const int n = y * P.nx + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        float rp = 0.f, rt = 0.f;
+        if constexpr (kRef<S>) {
+            const int s = ref_source(P, x, y, i);
+            rp = ref[s];
+            rt = ref[pl + s];
+        }
+        f[i] = S::ld(A + i * pl, n, P.is_f, wq(i) * rp);
+        if constexpr (WANT_G) g[i] = S::ld(A + (9 + i) * pl, n, P.is_g, 0.f);
+        h[i] = S::ld(A + (18 + i) * pl, n, P.is_h, wq(i) * rt);
+    }
+}
+
+// Shared staging of phi, T, 1/(rho c_p) and pre-collision h for a tile and its ring.
+template <int BX, int BY>
+struct RingSmem {
+    static constexpr int SX = BX + 2, SY = BY + 2, SN = SX * SY;
+    float phi[SN];
+    float T[SN];
+    float irc[SN];
+    float h[9][SN];
+};
+
+// Collide the node's populations and push them to their destinations, with every
+// boundary rule.  hold(i, k) and irc(k) give the pre-collision h_i and 1/(rho c_p)
+// of the node in ring slot k; phiR(k), TR(k) its phi and T.
+template <class S, int SX, class HOLD, class IRC, class PHIR, class TR>
+__device__ __forceinline__ void collide_push(const DevParams& P, typename S::elem* __restrict__ B, int x, int y,
+                                             int kown, bool interior, const Macro& m, float* f, float* g,
+                                             float* h, HOLD hold, IRC irc, PHIR phiR, TR TR_)
+{
+    const long long pl = P.plane;
+    const int n = y * P.nx + x;
+    node_collide(P, m, f, g, h);
+    // FP16 references: the writer's own rest equilibrium
+    const float rp = kRef<S> ? m.phi : 0.f, rt = kRef<S> ? m.T : 0.f;
+    if (interior) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int d = n + cy(i) * P.nx + cx(i);
+            const int kd = kown + cy(i) * SX + cx(i);
+            S::st(B + i * pl, d, f[i], P.s_f, wq(i) * rp);
+            S::st(B + (9 + i) * pl, d, g[i], P.s_g, 0.f);
+            const float ho = hold(i, kd);
+            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, wq(i) * rt);
+        }
+        return;
+    }
+    const float irc_own = irc(kown);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int o = opp(i);
+        int dx = x + cx(i), dy = y + cy(i);
+        if (P.bc_x == 0) dx = wrap(dx, P.nx);
+        if (P.bc_y == 1) dy = wrap(dy, P.ny);
+        const bool out_y = dy < 0 || dy >= P.ny;
+        const bool out_x = dx < 0 || dx >= P.nx;
+        if (out_y) {
+            // halfway bounce-back of f and g; anti-bounce-back of h with the wall
+            // temperature at the link's crossing point
+            const float xc = (float)x + 0.5f * cx(i);
+            const float Tw = (cy(i) < 0) ? T_wall_bottom(P, xc) : T_wall_top(P, xc);
+            S::st(B + o * pl, n, f[i], P.s_f, wq(o) * rp);
+            S::st(B + (9 + o) * pl, n, g[i], P.s_g, 0.f);
+            const float ho = hold(o, kown);
+            const float hin = -h[i] + 2.f * wq(o) * Tw;
+            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, wq(o) * rt);
+        } else if (out_x && dx < 0) {
+            // velocity inlet: bounce-back carrying the inlet momentum and phi_in
+            const float ycr = (float)y + 0.5f + 0.5f * cy(i);
+            const float cu = cx(o) * u_inlet(P, ycr);
+            S::st(B + o * pl, n, f[i] + 2.f * wq(o) * P.phi_in * cu * kInvCs2, P.s_f, wq(o) * rp);
+            S::st(B + (9 + o) * pl, n, g[i] + 2.f * wq(o) * m.rho * cu * kInvCs2, P.s_g, 0.f);
+            const float ho = hold(o, kown);
+            const float hin = -h[i] + 2.f * wq(o) * P.T_in;
+            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, wq(o) * rt);
+        } else if (out_x) {
+            // outflow: pressure anti-bounce-back of g (f and h arrive by the copy below)
+            const float cu = cx(o) * m.ux + cy(o) * m.uy;
+            const float sym = P.p_out * kInvCs2 +
+                              m.rho * (0.5f * cu * cu * kInvCs2 * kInvCs2 - 0.5f * (m.ux * m.ux + m.uy * m.uy) * kInvCs2);
+            S::st(B + (9 + o) * pl, n, -g[i] + 2.f * wq(o) * sym, P.s_g, 0.f);
+        } else {
+            const int d = dy * P.nx + dx;
+            const int kd = kown + cy(i) * SX + cx(i);
+            S::st(B + i * pl, d, f[i], P.s_f, wq(i) * rp);
+            S::st(B + (9 + i) * pl, d, g[i], P.s_g, 0.f);
+            const float ho = hold(i, kd);
+            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, wq(i) * rt);
+        }
+        // zero-gradient outflow of f and h: the ghost column beyond x = nx-1 carries the
+        // post-collision populations of the last column.  The destination decodes them
+        // with its own reference (their source lies outside), so encode with it.
+        if (P.bc_x == 1 && x == P.nx - 1 && cx(i) < 0) {
+            const int ey = y + cy(i);
+            if (ey >= 0 && ey < P.ny) {
+                const int d = ey * P.nx + x;
+                const int kd = kown + cy(i) * SX;
+                S::st(B + i * pl, d, f[i], P.s_f, kRef<S> ? wq(i) * phiR(kd) : 0.f);
+                const float ho = hold(i, kd);
+                S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, kRef<S> ? wq(i) * TR_(kd) : 0.f);
+            }
+        }
+    }
+}
+
+// One tile through the general path: thread loads, ghost values and every boundary
+// rule.  Used for lattices whose rows do not meet TMA alignment and for the tiles
+// along the lattice edges.  (bx, by): tile coordinates.
+template <int BX, int BY, class S>
+__device__ __forceinline__ void step_tile_general(const DevParams& P, const typename S::elem* __restrict__ A,
+                                                  typename S::elem* __restrict__ B, float* __restrict__ phiu,
+                                                  const float* __restrict__ refA, float* __restrict__ refB,
+                                                  RingSmem<BX, BY>& sm, int bx, int by)
+{
+    constexpr int SX = RingSmem<BX, BY>::SX, SN = RingSmem<BX, BY>::SN;
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    const int x0 = bx * BX, y0 = by * BY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < P.nx && y < P.ny;
+    const long long pl = P.plane;
+    const int n = y * P.nx + x;
+    const int kown = (ty + 1) * SX + tx + 1;
+    const bool interior = x0 >= 1 && x0 + BX <= P.nx - 1 && y0 >= 1 && y0 + BY <= P.ny - 1;
+
+    float f[9], g[9], h[9];
+    if (active) {
+        load_node<S>(P, A, refA, x, y, f, g, h);
+        float sf = 0.f, sh = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            sf += f[i];
+            sh += h[i];
+        }
+        sm.phi[kown] = sf;
+        sm.T[kown] = sh;
+        sm.irc[kown] = 1.f / fmaf(P.rcp_b, clamp1(sf), P.rcp_a);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sm.h[i][kown] = h[i];
+    }
+    auto get = [&](int gx, int gy, float& ph, float& tt) {
+        float a[9], c[9];
+        load_node<S, false>(P, A, refA, gx, gy, a, nullptr, c);
+        float sf = 0.f, sh = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            sf += a[i];
+            sh += c[i];
+        }
+        ph = sf;
+        tt = sh;
+    };
+    for (int k = threadIdx.x; k < SN; k += BX * BY) {
+        const int lx = k % SX, ly = k / SX;
+        const bool own = lx >= 1 && lx <= BX && ly >= 1 && ly <= BY && (x0 + lx - 1) < P.nx && (y0 + ly - 1) < P.ny;
+        if (own) continue;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        int wx = gx, wy = gy;
+        if (P.bc_x == 0) wx = wrap(wx, P.nx);
+        if (P.bc_y == 1) wy = wrap(wy, P.ny);
+        const bool far = gx < -1 || gx > P.nx || gy < -1 || gy > P.ny;
+        if (far) {
+            sm.phi[k] = 0.f;
+            sm.T[k] = 0.f;
+            sm.irc[k] = 0.f;
+            continue;
+        }
+        if (wx >= 0 && wx < P.nx && wy >= 0 && wy < P.ny) {
+            float a[9], c[9];
+            load_node<S, false>(P, A, refA, wx, wy, a, nullptr, c);
+            float sf = 0.f, sh = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                sf += a[i];
+                sh += c[i];
+                sm.h[i][k] = c[i];
+            }
+            sm.phi[k] = sf;
+            sm.T[k] = sh;
+            sm.irc[k] = 1.f / fmaf(P.rcp_b, clamp1(sf), P.rcp_a);
+        } else {
+            float ph, tt;
+            phiT_at(P, gx, gy, get, ph, tt);
+            sm.phi[k] = ph;
+            sm.T[k] = tt;
+            sm.irc[k] = 0.f;
+        }
+    }
+    __syncthreads();
+    if (active) {
+        float phin[9], Tn[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int k = kown + cy(i) * SX + cx(i);
+            phin[i] = sm.phi[k];
+            Tn[i] = sm.T[k];
+        }
+        const Macro m = node_macro(P, f, g, h, phin, Tn, phiu[n], phiu[pl + n]);
+        phiu[n] = m.phi * m.ux;
+        phiu[pl + n] = m.phi * m.uy;
+        if constexpr (kRef<S>) {
+            refB[n] = m.phi;
+            refB[pl + n] = m.T;
+        }
+        collide_push<S, SX>(
+            P, B, x, y, kown, interior, m, f, g, h, [&](int i, int k) { return sm.h[i][k]; },
+            [&](int k) { return sm.irc[k]; }, [&](int k) { return sm.phi[k]; }, [&](int k) { return sm.T[k]; });
+    }
+    __syncthreads();  // the caller may reuse sm for the next tile
+}
+
+template <int BX, int BY, class S>
+__global__ void __launch_bounds__(BX * BY, 3)
+k_step_general(const DevParams P, const typename S::elem* __restrict__ A, typename S::elem* __restrict__ B,
+               float* __restrict__ phiu, const float* __restrict__ refA, float* __restrict__ refB)
+{
+    __shared__ RingSmem<BX, BY> sm;
+    step_tile_general<BX, BY, S>(P, A, B, phiu, refA, refB, sm, blockIdx.x, blockIdx.y);
+}
+
+// ------------------------------------------------------------ TMA kernel
+//
+// Persistent CTAs walk a tile list: first the TMA tiles (tile and halo inside the
+// lattice: x0 >= XP, x0 + BX + XP <= nx, y0 >= 2, y0 + BY + 2 <= ny), then the edge
+// tiles through the general path.  For a TMA tile one elected thread issues 3D bulk
+// tensor copies (cp.async.bulk.tensor) of the 9 f planes and the 9 h planes over the
+// tile plus a one-node ring (widened to XP columns each side for the 16-byte rule),
+// the 9 g planes and the 2 (phi u) planes over the tile, and for FP16 the 2 reference
+// planes over the tile plus a two-node ring, all completing on one mbarrier.  While a
+// tile is computed, the next tile's copies are in flight into the other stage.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// bounded wait: false after about 2^22 polls (each try_wait suspends for a while)
+constexpr uint32_t kWaitLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int BX, int BY, class S>
+struct TmaLayout {
+    using E = typename S::elem;
+    static constexpr int XP = 16 / (int)sizeof(E);           // column pad for 16-byte aligned boxes
+    static constexpr int FW = BX + 2 * XP, FH = BY + 2;     // f/h box (tile + ring, widened)
+    static constexpr int RW = BX + 8, RH = BY + 4;          // reference box (tile + 2-ring, widened)
+    static constexpr int rnd(int b) { return (b + 127) / 128 * 128; }
+    static constexpr int F_BYTES = 9 * FH * FW * (int)sizeof(E);
+    static constexpr int G_BYTES = 9 * BY * BX * (int)sizeof(E);
+    static constexpr int U_BYTES = 2 * BY * BX * 4;
+    static constexpr int R_BYTES = kRef<S> ? 2 * RH * RW * 4 : 0;
+    static constexpr int OFF_F = 0, OFF_H = rnd(F_BYTES), OFF_G = OFF_H + rnd(F_BYTES), OFF_U = OFF_G + rnd(G_BYTES),
+                         OFF_R = OFF_U + rnd(U_BYTES), STAGE = OFF_R + rnd(R_BYTES);
+    static constexpr uint32_t TX_BYTES = 2 * F_BYTES + G_BYTES + U_BYTES + R_BYTES;
+};
+
+struct TmaMaps {
+    CUtensorMap popF;  // populations, box FW x FH x 9 (used for f at z = 0 and h at z = 18)
+    CUtensorMap popG;  // populations, box BX x BY x 9 (g at z = 9)
+    CUtensorMap phiu;  // (phi u) planes, box BX x BY x 2
+    CUtensorMap ref;   // FP16 references, box RW x RH x 2
+};
+
+template <int BX, int BY, class S>
+__global__ void __launch_bounds__(BX * BY, 2)
+k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typename S::elem* __restrict__ A,
+           typename S::elem* __restrict__ B, float* __restrict__ phiu, const float* __restrict__ refA,
+           float* __restrict__ refB, int bx0, int by0, int ntbx, int ntby, int* __restrict__ err)
+{
+    using L = TmaLayout<BX, BY, S>;
+    using E = typename S::elem;
+    constexpr int SX = BX + 2, SN = SX * (BY + 2);
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ RingSmem<BX, BY> sm;
+
+    const int ntma = ntbx * ntby;  // TMA tiles: bx in [bx0, bx0 + ntbx), by in [by0, by0 + ntby)
+    const int tilesx = (P.nx + BX - 1) / BX, tilesy = (P.ny + BY - 1) / BY;
+    const int nall = tilesx * tilesy;
+    const int nedge = nall - ntma;
+    const int tid = threadIdx.x;
+    const long long pl = P.plane;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int t, int s) {
+        const int bx = bx0 + t % ntbx, by = by0 + t / ntbx;
+        const int x0 = bx * BX, y0 = by * BY;
+        unsigned char* st = dsm + s * L::STAGE;
+        fence_proxy_async();
+        mbar_expect_tx(&bar[s], L::TX_BYTES);
+        tma_load_3d(st + L::OFF_F, &maps.popF, &bar[s], x0 - L::XP, y0 - 1, 0);
+        tma_load_3d(st + L::OFF_H, &maps.popF, &bar[s], x0 - L::XP, y0 - 1, 18);
+        tma_load_3d(st + L::OFF_G, &maps.popG, &bar[s], x0, y0, 9);
+        tma_load_3d(st + L::OFF_U, &maps.phiu, &bar[s], x0, y0, 0);
+        if constexpr (kRef<S>) tma_load_3d(st + L::OFF_R, &maps.ref, &bar[s], x0 - 4, y0 - 2, 0);
+    };
+
+    int it = 0;
+    int t = blockIdx.x;
+    if (t < ntma && tid == 0) issue(t, 0);
+    for (; t < ntma; t += gridDim.x, ++it) {
+        const int s = it & 1;
+        const int tn = t + gridDim.x;
+        if (tn < ntma && tid == 0) issue(tn, s ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // let this CTA's other copy land (bounded) before leaving
+                if (tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const unsigned char* st = dsm + s * L::STAGE;
+        const E* sF = (const E*)(st + L::OFF_F);
+        const E* sH = (const E*)(st + L::OFF_H);
+        const E* sG = (const E*)(st + L::OFF_G);
+        const float* sU = (const float*)(st + L::OFF_U);
+        const float* sR = (const float*)(st + L::OFF_R);
+        const int bx = bx0 + t % ntbx, by = by0 + t / ntbx;
+        const int x0 = bx * BX, y0 = by * BY;
+
+        // decoded population i of ring slot (lx, ly) from the f (or h) box
+        auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly) {
+            const float raw = S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, 0.f);
+            if constexpr (kRef<S>) {
+                const float r = sR[(rplane * L::RH + ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i)];
+                return fmaf(wq(i), r, raw);
+            } else {
+                return raw;
+            }
+        };
+
+        // phi, T, 1/(rho c_p) of the tile and its ring
+        for (int k = tid; k < SN; k += BX * BY) {
+            const int lx = k % SX, ly = k / SX;
+            float sf = 0.f, sh = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                sf += decF(sF, P.is_f, 0, i, lx, ly);
+                sh += decF(sH, P.is_h, 1, i, lx, ly);
+            }
+            sm.phi[k] = sf;
+            sm.T[k] = sh;
+            sm.irc[k] = 1.f / fmaf(P.rcp_b, clamp1(sf), P.rcp_a);
+        }
+        __syncthreads();
+
+        const int tx = tid % BX, ty = tid / BX;
+        const int lx = tx + 1, ly = ty + 1, kown = ly * SX + lx;
+        const int x = x0 + tx, y = y0 + ty;
+        const int n = y * P.nx + x;
+        float f[9], g[9], h[9], phin[9], Tn[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            f[i] = decF(sF, P.is_f, 0, i, lx, ly);
+            h[i] = decF(sH, P.is_h, 1, i, lx, ly);
+            g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, 0.f);
+            const int k = kown + cy(i) * SX + cx(i);
+            phin[i] = sm.phi[k];
+            Tn[i] = sm.T[k];
+        }
+        const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
+        phiu[n] = m.phi * m.ux;
+        phiu[pl + n] = m.phi * m.uy;
+        if constexpr (kRef<S>) {
+            refB[n] = m.phi;
+            refB[pl + n] = m.T;
+        }
+        collide_push<S, SX>(
+            P, B, x, y, kown, true, m, f, g, h,
+            [&](int i, int kd) { return decF(sH, P.is_h, 1, i, kd % SX, kd / SX); },
+            [&](int kd) { return sm.irc[kd]; }, [&](int kd) { return sm.phi[kd]; },
+            [&](int kd) { return sm.T[kd]; });
+        __syncthreads();  // stage s and sm are free for the copies issued next iteration
+    }
+
+    // edge tiles through the general path, continuing this CTA's round-robin share
+    for (int e = t - ntma; e < nedge; e += gridDim.x) {
+        // map edge index e to the e-th tile outside the TMA rectangle
+        int idx = e, bx = 0, by = 0;
+        {
+            // tiles in row-major order, skipping the TMA rectangle
+            int row = 0;
+            for (row = 0; row < tilesy; ++row) {
+                const bool inner = row >= by0 && row < by0 + ntby;
+                const int cnt = inner ? tilesx - ntbx : tilesx;
+                if (idx < cnt) break;
+                idx -= cnt;
+            }
+            by = row;
+            const bool inner = by >= by0 && by < by0 + ntby;
+            bx = (inner && idx >= bx0) ? idx + ntbx : idx;
+        }
+        step_tile_general<BX, BY, S>(P, A, B, phiu, refA, refB, sm, bx, by);
+    }
+}
+
+}  // namespace tpf

@@ -1,222 +1,47 @@
-// Kernels and C-ABI of the tpflbm library (declarations and conventions in
-// include/tpflbm.h).  One fused kernel advances the three coupled D2Q9 LBEs of
-// arXiv 2306.11320 by one time step; the others initialise, read back and reduce.
+// C-ABI of the tpflbm library (declarations and conventions in include/tpflbm.h)
+// and the auxiliary kernels: initialisation, field read-back, state I/O and FP64
+// reductions.  The step kernels live in step.cuh.
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
-#include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "../../include/tpflbm.h"
 #include "lattice.cuh"
+#include "step.cuh"
 
 using namespace tpf;
 
 namespace {
 
-// ------------------------------------------------------------- step kernel
-//
-// Push scheme on pre-collision state.  A CTA owns a BX x BY tile of nodes (one
-// node per thread) and stages, for the tile plus a one-node ring, phi = sum f_i,
-// T = sum h_i (ghost rules applied) and the pre-collision h_i in shared memory.
-// Each thread then computes its node's macroscopic state (stencils from shared
-// memory), collides the three LBEs, and writes every post-collision population to
-// the node it streams to in buffer B.  The thermal update of Eq. 28 needs the
-// destination's own h_i(y, t) and rho c_p(y), both found in shared memory because
-// every destination lies in the tile or its ring.  Populations leaving through a
-// wall, the inlet or the outflow plane are reflected into the node itself with the
-// corresponding rule.  Every (direction, node) slot of B is written exactly once.
-
-template <int BX, int BY, class S>
-__global__ void __launch_bounds__(BX * BY)
-k_step(const DevParams P, const typename S::elem* __restrict__ A, typename S::elem* __restrict__ B,
-       float* __restrict__ phiu)
-{
-    constexpr int SX = BX + 2, SY = BY + 2, SN = SX * SY;
-    __shared__ float s_phi[SN];
-    __shared__ float s_T[SN];
-    __shared__ float s_h[9][SN];
-
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * BX + tx;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < P.nx && y < P.ny;
-    const long long pl = P.plane;
-    const long long n = (long long)y * P.nx + x;
-
-    float f[9], g[9], h[9];
-    if (active) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            f[i] = S::ld(A, i * pl + n, P.is_f, 0.f);
-            g[i] = S::ld(A, (9 + i) * pl + n, P.is_g, 0.f);
-            h[i] = S::ld(A, (18 + i) * pl + n, P.is_h, wq(i) * P.X_h);
-        }
-        float sf = 0.f, sh = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            sf += f[i];
-            sh += h[i];
-        }
-        const int k = (ty + 1) * SX + tx + 1;
-        s_phi[k] = sf;
-        s_T[k] = sh;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) s_h[i][k] = h[i];
-    }
-
-    // phi, T and h of an interior node read straight from A
-    auto get = [&](int gx, int gy, float& ph, float& tt) {
-        const long long m = (long long)gy * P.nx + gx;
-        float sf = 0.f, sh = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            sf += S::ld(A, i * pl + m, P.is_f, 0.f);
-            sh += S::ld(A, (18 + i) * pl + m, P.is_h, wq(i) * P.X_h);
-        }
-        ph = sf;
-        tt = sh;
-    };
-
-    // ring (and the unused part of ragged tiles)
-    for (int k = tid; k < SN; k += BX * BY) {
-        const int lx = k % SX, ly = k / SX;
-        const bool own = lx >= 1 && lx <= BX && ly >= 1 && ly <= BY &&
-                         (x0 + lx - 1) < P.nx && (y0 + ly - 1) < P.ny;
-        if (own) continue;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        int wx = gx, wy = gy;
-        if (P.bc_x == 0) wx = wrap(wx, P.nx);
-        if (P.bc_y == 1) wy = wrap(wy, P.ny);
-        const bool far = gx < -1 || gx > P.nx || gy < -1 || gy > P.ny;
-        if (far) {
-            s_phi[k] = 0.f;
-            s_T[k] = 0.f;
-            continue;
-        }
-        if (wx >= 0 && wx < P.nx && wy >= 0 && wy < P.ny) {
-            const long long m = (long long)wy * P.nx + wx;
-            float sf = 0.f, sh = 0.f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                sf += S::ld(A, i * pl + m, P.is_f, 0.f);
-                const float hv = S::ld(A, (18 + i) * pl + m, P.is_h, wq(i) * P.X_h);
-                sh += hv;
-                s_h[i][k] = hv;
-            }
-            s_phi[k] = sf;
-            s_T[k] = sh;
-        } else {
-            float ph, tt;
-            phiT_at(P, gx, gy, get, ph, tt);
-            s_phi[k] = ph;
-            s_T[k] = tt;
-        }
-    }
-    __syncthreads();
-    if (!active) return;
-
-    const int lx = tx + 1, ly = ty + 1;
-    float phin[9], Tn[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int k = (ly + cy(i)) * SX + lx + cx(i);
-        phin[i] = s_phi[k];
-        Tn[i] = s_T[k];
-    }
-    const float pux = phiu[n], puy = phiu[pl + n];
-    const Macro m = node_macro(P, f, g, h, phin, Tn, pux, puy);
-    phiu[n] = m.phi * m.ux;
-    phiu[pl + n] = m.phi * m.uy;
-
-    node_collide(P, m, f, g, h);
-
-    // streaming with the boundary rules
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int o = opp(i);
-        int dx = x + cx(i), dy = y + cy(i);
-        if (P.bc_x == 0) dx = wrap(dx, P.nx);
-        if (P.bc_y == 1) dy = wrap(dy, P.ny);
-        const bool out_y = dy < 0 || dy >= P.ny;
-        const bool out_x = dx < 0 || dx >= P.nx;
-        if (out_y) {
-            // halfway bounce-back of f and g; anti-bounce-back of h with the wall
-            // temperature at the link's crossing point
-            const float xc = (float)x + 0.5f * cx(i);
-            const float Tw = (cy(i) < 0) ? T_wall_bottom(P, xc) : T_wall_top(P, xc);
-            S::st(B, o * pl + n, f[i], P.s_f, 0.f);
-            S::st(B, (9 + o) * pl + n, g[i], P.s_g, 0.f);
-            const float hold = s_h[o][ly * SX + lx];
-            const float hin = -h[i] + 2.f * wq(o) * Tw;
-            S::st(B, (18 + o) * pl + n, hold + (hin - hold) / m.rcp, P.s_h, wq(o) * P.X_h);
-        } else if (out_x && dx < 0) {
-            // velocity inlet: bounce-back carrying the inlet momentum and phi_in
-            const float ycr = (float)y + 0.5f + 0.5f * cy(i);
-            const float cu = cx(o) * u_inlet(P, ycr);
-            S::st(B, o * pl + n, f[i] + 2.f * wq(o) * P.phi_in * cu * kInvCs2, P.s_f, 0.f);
-            S::st(B, (9 + o) * pl + n, g[i] + 2.f * wq(o) * m.rho * cu * kInvCs2, P.s_g, 0.f);
-            const float hold = s_h[o][ly * SX + lx];
-            const float hin = -h[i] + 2.f * wq(o) * P.T_in;
-            S::st(B, (18 + o) * pl + n, hold + (hin - hold) / m.rcp, P.s_h, wq(o) * P.X_h);
-        } else if (out_x) {
-            // outflow: pressure anti-bounce-back of g (f and h arrive by the copy below)
-            const float cu = cx(o) * m.ux + cy(o) * m.uy;
-            const float sym = P.p_out * kInvCs2 +
-                              m.rho * (0.5f * cu * cu * kInvCs2 * kInvCs2 - 0.5f * (m.ux * m.ux + m.uy * m.uy) * kInvCs2);
-            S::st(B, (9 + o) * pl + n, -g[i] + 2.f * wq(o) * sym, P.s_g, 0.f);
-        } else {
-            const long long d = (long long)dy * P.nx + dx;
-            S::st(B, i * pl + d, f[i], P.s_f, 0.f);
-            S::st(B, (9 + i) * pl + d, g[i], P.s_g, 0.f);
-            const int kd = (ly + cy(i)) * SX + lx + cx(i);
-            const float rcp_d = fmaf(P.rcp_b, clamp1(s_phi[kd]), P.rcp_a);
-            const float hold = s_h[i][kd];
-            S::st(B, (18 + i) * pl + d, hold + (h[i] - hold) / rcp_d, P.s_h, wq(i) * P.X_h);
-        }
-        // zero-gradient outflow of f and h: the ghost column beyond x = nx-1 carries
-        // the post-collision populations of the last column
-        if (P.bc_x == 1 && x == P.nx - 1 && cx(i) < 0) {
-            const int ey = y + cy(i);
-            if (ey >= 0 && ey < P.ny) {
-                const long long d = (long long)ey * P.nx + x;
-                S::st(B, i * pl + d, f[i], P.s_f, 0.f);
-                const int kd = (ly + cy(i)) * SX + lx;
-                const float rcp_d = fmaf(P.rcp_b, clamp1(s_phi[kd]), P.rcp_a);
-                const float hold = s_h[i][kd];
-                S::st(B, (18 + i) * pl + d, hold + (h[i] - hold) / rcp_d, P.s_h, wq(i) * P.X_h);
-            }
-        }
-    }
-}
+constexpr int kBX = 32, kBY = 8;
 
 // ------------------------------------------------------- auxiliary kernels
 
 // Macroscopic state of node (x, y) read straight from global memory.
 template <class S>
 __device__ Macro macro_at(const DevParams& P, const typename S::elem* __restrict__ A,
-                          const float* __restrict__ phiu, int x, int y)
+                          const float* __restrict__ ref, const float* __restrict__ phiu, int x, int y)
 {
     const long long pl = P.plane;
-    const long long n = (long long)y * P.nx + x;
+    const int n = y * P.nx + x;
     float f[9], g[9], h[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        f[i] = S::ld(A, i * pl + n, P.is_f, 0.f);
-        g[i] = S::ld(A, (9 + i) * pl + n, P.is_g, 0.f);
-        h[i] = S::ld(A, (18 + i) * pl + n, P.is_h, wq(i) * P.X_h);
-    }
+    load_node<S>(P, A, ref, x, y, f, g, h);
     auto get = [&](int gx, int gy, float& ph, float& tt) {
-        const long long m = (long long)gy * P.nx + gx;
+        float a[9], c[9];
+        load_node<S, false>(P, A, ref, gx, gy, a, nullptr, c);
         float sf = 0.f, sh = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            sf += S::ld(A, i * pl + m, P.is_f, 0.f);
-            sh += S::ld(A, (18 + i) * pl + m, P.is_h, wq(i) * P.X_h);
+            sf += a[i];
+            sh += c[i];
         }
         ph = sf;
         tt = sh;
@@ -228,14 +53,14 @@ __device__ Macro macro_at(const DevParams& P, const typename S::elem* __restrict
 }
 
 template <class S>
-__global__ void k_fields(const DevParams P, const typename S::elem* __restrict__ A,
+__global__ void k_fields(const DevParams P, const typename S::elem* __restrict__ A, const float* __restrict__ ref,
                          const float* __restrict__ phiu, float* __restrict__ out)
 {
     const long long N = (long long)P.nx * P.ny;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % P.nx), y = (int)(n / P.nx);
-        const Macro m = macro_at<S>(P, A, phiu, x, y);
+        const Macro m = macro_at<S>(P, A, ref, phiu, x, y);
         out[n] = m.phi;
         out[P.plane + n] = m.ux;
         out[2 * P.plane + n] = m.uy;
@@ -244,46 +69,90 @@ __global__ void k_fields(const DevParams P, const typename S::elem* __restrict__
     }
 }
 
+// Equilibrium populations from the staged fields (planes 0-4: phi, ux, uy, p, T).
+// FP16 references: phi and T of each node (ref planes), each population encoded
+// against its reference node (ref_source).
 template <class S>
 __global__ void k_init(const DevParams P, const float* __restrict__ in, typename S::elem* __restrict__ A,
-                       float* __restrict__ phiu)
+                       float* __restrict__ ref, float* __restrict__ phiu)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % P.nx), y = (int)(n / P.nx);
         const float phi = in[n], ux = in[pl + n], uy = in[2 * pl + n], p = in[3 * pl + n], T = in[4 * pl + n];
         float f[9], g[9], h[9];
         node_equilibria(P, phi, ux, uy, p, T, f, g, h);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            S::st(A, i * pl + n, f[i], P.s_f, 0.f);
-            S::st(A, (9 + i) * pl + n, g[i], P.s_g, 0.f);
-            S::st(A, (18 + i) * pl + n, h[i], P.s_h, wq(i) * P.X_h);
+            float rp = 0.f, rt = 0.f;
+            if constexpr (kRef<S>) {
+                const int s = ref_source(P, x, y, i);
+                rp = in[s];
+                rt = in[4 * pl + s];
+            }
+            S::st(A + i * pl, n, f[i], P.s_f, wq(i) * rp);
+            S::st(A + (9 + i) * pl, n, g[i], P.s_g, 0.f);
+            S::st(A + (18 + i) * pl, n, h[i], P.s_h, wq(i) * rt);
+        }
+        if constexpr (kRef<S>) {
+            ref[n] = phi;
+            ref[pl + n] = T;
         }
         phiu[n] = phi * ux;
         phiu[pl + n] = phi * uy;
     }
 }
 
-// Convert one population plane between float32 staging and the storage format.
-template <class S>
-__global__ void k_plane_encode(const DevParams P, const float* __restrict__ in, typename S::elem* __restrict__ out,
-                               float s, float ref)
+// State I/O of one LBE (k = 0 f, 1 g, 2 h) between 9 float32 staging planes and
+// storage.  For FP16, k_lbe_ref first sets each node's reference to the zeroth
+// moment of its staged populations (phi for f, T for h).
+__global__ void k_lbe_ref(const DevParams P, int k, const float* __restrict__ in, float* __restrict__ ref)
 {
     const long long N = (long long)P.nx * P.ny;
+    const long long pl = P.plane;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x)
-        S::st(out, n, in[n], s, ref);
+         n += (long long)gridDim.x * blockDim.x) {
+        float r = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r += in[i * pl + n];
+        ref[(k == 2 ? pl : 0) + n] = r;
+    }
 }
 template <class S>
-__global__ void k_plane_decode(const DevParams P, const typename S::elem* __restrict__ in, float* __restrict__ out,
-                               float is, float ref)
+__global__ void k_lbe_encode(const DevParams P, int k, const float* __restrict__ in, typename S::elem* __restrict__ A,
+                             const float* __restrict__ ref)
 {
     const long long N = (long long)P.nx * P.ny;
+    const long long pl = P.plane;
+    const float s = k == 0 ? P.s_f : (k == 1 ? P.s_g : P.s_h);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x)
-        out[n] = S::ld(in, n, is, ref);
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % P.nx), y = (int)(n / P.nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float r = (kRef<S> && k != 1) ? ref[(k == 2 ? pl : 0) + ref_source(P, x, y, i)] : 0.f;
+            S::st(A + (9 * k + i) * pl, n, in[i * pl + n], s, wq(i) * r);
+        }
+    }
+}
+template <class S>
+__global__ void k_lbe_decode(const DevParams P, int k, const typename S::elem* __restrict__ A,
+                             const float* __restrict__ ref, float* __restrict__ out)
+{
+    const long long N = (long long)P.nx * P.ny;
+    const long long pl = P.plane;
+    const float is = k == 0 ? P.is_f : (k == 1 ? P.is_g : P.is_h);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % P.nx), y = (int)(n / P.nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float r = (kRef<S> && k != 1) ? ref[(k == 2 ? pl : 0) + ref_source(P, x, y, i)] : 0.f;
+            out[i * pl + n] = S::ld(A + (9 * k + i) * pl, n, is, wq(i) * r);
+        }
+    }
 }
 
 // FP64 reductions (see tpflbm_diagnostics).  Each block writes 8 partial sums;
@@ -293,15 +162,15 @@ constexpr int kRedMaxBlocks = 1024;
 
 template <class S>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_partial(const DevParams P, const typename S::elem* __restrict__ A, const float* __restrict__ phiu,
-                 double* __restrict__ partial)
+k_reduce_partial(const DevParams P, const typename S::elem* __restrict__ A, const float* __restrict__ ref,
+                 const float* __restrict__ phiu, double* __restrict__ partial)
 {
     const long long N = (long long)P.nx * P.ny;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % P.nx), y = (int)(n / P.nx);
-        const Macro m = macro_at<S>(P, A, phiu, x, y);
+        const Macro m = macro_at<S>(P, A, ref, phiu, x, y);
         acc[0] += m.phi;
         acc[1] += (double)m.rcp * m.T;
         acc[2] += m.T;
@@ -347,51 +216,62 @@ struct tpflbm {
     tpflbm_params hp{};
     DevParams dp{};
     int device = 0;
+    int num_sms = 0;
     cudaStream_t stream = nullptr;
     bool owns = false;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    void* popA = nullptr;
-    void* popB = nullptr;
+    void* pop[2] = {nullptr, nullptr};  // population buffers; pop[cur] holds time t
+    float* ref[2] = {nullptr, nullptr}; // FP16 references, paired with pop
+    int cur = 0;
     float* phiu = nullptr;
-    float* fields = nullptr;  // 5 planes of float staging
-    double* red = nullptr;    // kRedMaxBlocks * 8 partials + 8 results
+    float* stage = nullptr;             // 9 float planes: fields and state I/O
+    double* red = nullptr;              // kRedMaxBlocks * 8 partials + 8 results
+    int* err = nullptr;                 // device error flag of the step kernels
+    // TMA step kernel
+    bool tma = false;
+    TmaMaps maps[2]{};                  // maps[c]: reading pop[c]
+    int bx0 = 0, by0 = 0, ntbx = 0, ntby = 0, grid_tma = 0;
     long long t = 0;
-    std::string err;
+    std::string err_msg;
 };
 
 namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kBX = 32, kBY = 8;
+constexpr int kStagePlanes = 9;
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 long long plane_of(int nx, int ny) { return (((long long)nx * ny + 63) / 64) * 64; }
 
 struct Layout {
-    size_t popA, popB, phiu, fields, red, total;
+    size_t pop0, pop1, ref0, ref1, phiu, stage, red, err, total;
 };
 
 Layout layout_of(int nx, int ny, int storage)
 {
     const long long pl = plane_of(nx, ny);
-    const size_t e = storage == TPF_STORAGE_FP16 ? 2 : 4;
+    const bool f16 = storage == TPF_STORAGE_FP16;
+    const size_t e = f16 ? 2 : 4;
     Layout L{};
     size_t off = 0;
-    L.popA = off; off = align256(off + 27 * (size_t)pl * e);
-    L.popB = off; off = align256(off + 27 * (size_t)pl * e);
+    L.pop0 = off; off = align256(off + 27 * (size_t)pl * e);
+    L.pop1 = off; off = align256(off + 27 * (size_t)pl * e);
+    L.ref0 = off; off = align256(off + (f16 ? 2 * (size_t)pl * 4 : 0));
+    L.ref1 = off; off = align256(off + (f16 ? 2 * (size_t)pl * 4 : 0));
     L.phiu = off; off = align256(off + 2 * (size_t)pl * 4);
-    L.fields = off; off = align256(off + 5 * (size_t)pl * 4);
+    L.stage = off; off = align256(off + kStagePlanes * (size_t)pl * 4);
     L.red = off; off = align256(off + (kRedMaxBlocks * 8 + 8) * sizeof(double));
+    L.err = off; off = align256(off + 256);
     L.total = off;
     return L;
 }
 
 int fail(tpflbm_t h, int code, const std::string& msg)
 {
-    if (h) h->err = msg;
+    if (h) h->err_msg = msg;
     else g_create_error = msg;
     return code;
 }
@@ -417,7 +297,7 @@ int validate(int nx, int ny, const tpflbm_params* p, std::string& why)
 {
     if (!p) { why = "params is NULL"; return TPF_ERR_INVALID_ARG; }
     if (nx < 3 || ny < 3) { why = "nx and ny must be >= 3"; return TPF_ERR_INVALID_ARG; }
-    if ((long long)nx * ny > (1LL << 31)) { why = "lattice too large"; return TPF_ERR_INVALID_ARG; }
+    if ((long long)nx * ny > (1LL << 30)) { why = "lattice too large (nx * ny > 2^30)"; return TPF_ERR_INVALID_ARG; }
     if (p->storage != TPF_STORAGE_FP32 && p->storage != TPF_STORAGE_FP16) { why = "unknown storage"; return TPF_ERR_INVALID_ARG; }
     if (p->bc_x < 0 || p->bc_x > 1 || p->bc_y < 0 || p->bc_y > 1) { why = "bc_x/bc_y must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
     if (p->sigma_law < 0 || p->sigma_law > 1) { why = "sigma_law must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
@@ -426,6 +306,7 @@ int validate(int nx, int ny, const tpflbm_params* p, std::string& why)
     if (!(p->cp_l > 0 && p->cp_h > 0)) { why = "heat capacities must be positive"; return TPF_ERR_INVALID_ARG; }
     if (!(p->M_phi > 0) || !(p->W > 0)) { why = "M_phi and W must be positive"; return TPF_ERR_INVALID_ARG; }
     if (p->bc_x == 1 && p->bc_y == 1) { why = "an inlet/outflow channel needs walls (bc_y = 0)"; return TPF_ERR_INVALID_ARG; }
+    if (p->fp16_scale_f < 0 || p->fp16_scale_g < 0 || p->fp16_scale_h < 0) { why = "FP16 scales must be >= 0"; return TPF_ERR_INVALID_ARG; }
     return TPF_OK;
 }
 
@@ -453,13 +334,11 @@ DevParams make_dev_params(int nx, int ny, const tpflbm_params& p)
     d.T_bot = (float)p.T_bot; d.T_bot_amp = (float)p.T_bot_amp; d.T_bot_k = (float)p.T_bot_k;
     d.T_bot_slope = (float)p.T_bot_slope; d.T_top = (float)p.T_top; d.T_top_slope = (float)p.T_top_slope;
     if (p.storage == TPF_STORAGE_FP16) {
-        d.s_f = pow2_scale(p.fp16_scale_f, 1.0);
+        d.s_f = pow2_scale(p.fp16_scale_f, 1024.0);
         d.s_g = pow2_scale(p.fp16_scale_g, 1024.0);
-        d.s_h = pow2_scale(p.fp16_scale_h, 1.0);
-        d.X_h = (float)p.fp16_ref_T;
+        d.s_h = pow2_scale(p.fp16_scale_h, 64.0);
     } else {
         d.s_f = d.s_g = d.s_h = 1.f;
-        d.X_h = 0.f;
     }
     d.is_f = 1.f / d.s_f; d.is_g = 1.f / d.s_g; d.is_h = 1.f / d.s_h;
     return d;
@@ -471,54 +350,156 @@ int grid_1d(long long N)
     return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
 }
 
+// ----------------------------------------------------------- TMA set-up
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, void* base, int nx, int ny, int nz,
+              long long plane, int bw, int bh, int bd)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)plane * esize};
+    cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bd};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class S>
+void setup_tma(tpflbm_t h)
+{
+    using L = TmaLayout<kBX, kBY, S>;
+    const int nx = h->nx, ny = h->ny;
+    const size_t e = sizeof(typename S::elem);
+    h->tma = false;
+    if (((size_t)nx * e) % 16 != 0 || ((size_t)nx * 4) % 16 != 0) return;
+    // TMA tiles: tile and its (widened) halo inside the lattice
+    const int bx_lo = (L::XP + kBX - 1) / kBX, by_lo = (2 + kBY - 1) / kBY;
+    int bx_hi = -1, by_hi = -1;  // last tile index with x0 + BX + XP <= nx (y0 + BY + 2 <= ny)
+    for (int b = 0; (b + 1) * kBX + L::XP <= nx; ++b) bx_hi = b;
+    for (int b = 0; (b + 1) * kBY + 2 <= ny; ++b) by_hi = b;
+    if (bx_hi < bx_lo || by_hi < by_lo) return;
+    h->bx0 = bx_lo; h->by0 = by_lo;
+    h->ntbx = bx_hi - bx_lo + 1; h->ntby = by_hi - by_lo + 1;
+    const CUtensorMapDataType dt = sizeof(typename S::elem) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const long long pl = h->dp.plane;
+    for (int c = 0; c < 2; ++c) {
+        TmaMaps& M = h->maps[c];
+        bool ok = make_map(&M.popF, dt, e, h->pop[c], nx, ny, 27, pl, L::FW, L::FH, 9) &&
+                  make_map(&M.popG, dt, e, h->pop[c], nx, ny, 27, pl, kBX, kBY, 9) &&
+                  make_map(&M.phiu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->phiu, nx, ny, 2, pl, kBX, kBY, 2);
+        if (kRef<S>) ok = ok && make_map(&M.ref, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->ref[c], nx, ny, 2, pl, L::RW, L::RH, 2);
+        else M.ref = M.phiu;
+        if (!ok) return;
+    }
+    const int smem = 2 * L::STAGE;
+    if (cudaFuncSetAttribute(k_step_tma<kBX, kBY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<kBX, kBY, S>, kBX * kBY, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return;
+    }
+    const int ntiles = ((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY);
+    h->grid_tma = std::min(ntiles, per_sm * h->num_sms);
+    h->tma = true;
+}
+
 int finish_create(tpflbm_t h, int nx, int ny, const tpflbm_params* p, void* ws, size_t bytes, bool owns)
 {
     h->nx = nx; h->ny = ny; h->hp = *p;
     h->dp = make_dev_params(nx, ny, *p);
     cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     const Layout L = layout_of(nx, ny, p->storage);
     h->ws = ws; h->ws_bytes = bytes; h->owns = owns;
     char* b = (char*)ws;
-    h->popA = b + L.popA;
-    h->popB = b + L.popB;
+    h->pop[0] = b + L.pop0;
+    h->pop[1] = b + L.pop1;
+    h->ref[0] = (float*)(b + L.ref0);
+    h->ref[1] = (float*)(b + L.ref1);
     h->phiu = (float*)(b + L.phiu);
-    h->fields = (float*)(b + L.fields);
+    h->stage = (float*)(b + L.stage);
     h->red = (double*)(b + L.red);
+    h->err = (int*)(b + L.err);
+    if (cudaMemset(h->err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "cudaMemset");
+    if (p->storage == TPF_STORAGE_FP16) setup_tma<StoreF16>(h);
+    else setup_tma<StoreF32>(h);
     return TPF_OK;
 }
 
 template <class S>
 void launch_step(tpflbm_t h)
 {
+    using E = typename S::elem;
     const DevParams& P = h->dp;
-    dim3 blk(kBX, kBY), grd((P.nx + kBX - 1) / kBX, (P.ny + kBY - 1) / kBY);
-    k_step<kBX, kBY, S><<<grd, blk, 0, h->stream>>>(P, (const typename S::elem*)h->popA,
-                                                  (typename S::elem*)h->popB, h->phiu);
-    std::swap(h->popA, h->popB);
+    const int c = h->cur;
+    const E* A = (const E*)h->pop[c];
+    E* B = (E*)h->pop[c ^ 1];
+    if (h->tma) {
+        using L = TmaLayout<kBX, kBY, S>;
+        k_step_tma<kBX, kBY, S><<<h->grid_tma, kBX * kBY, 2 * L::STAGE, h->stream>>>(
+            P, h->maps[c], A, B, h->phiu, h->ref[c], h->ref[c ^ 1], h->bx0, h->by0, h->ntbx, h->ntby, h->err);
+    } else {
+        dim3 grd((P.nx + kBX - 1) / kBX, (P.ny + kBY - 1) / kBY);
+        k_step_general<kBX, kBY, S><<<grd, kBX * kBY, 0, h->stream>>>(P, A, B, h->phiu, h->ref[c], h->ref[c ^ 1]);
+    }
+    h->cur ^= 1;
 }
 
-// copy a [ny][nx] float field (host or device) into staging plane k
+// error raised by a step kernel (bounded waits that ran out)
+int check_err(tpflbm_t h)
+{
+    int v = 0;
+    TPF_CUDA(h, cudaMemcpyAsync(&v, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (v) return fail(h, TPF_ERR_TIMEOUT, "a step kernel gave up waiting for its shared-memory copies");
+    return TPF_OK;
+}
+
+// copy a [ny][nx] float field (host or device, or NULL = constant `fill`) into staging plane k
 int stage_in(tpflbm_t h, const float* src, int k, float fill)
 {
     const long long N = (long long)h->nx * h->ny;
-    float* dst = h->fields + k * h->dp.plane;
-    if (!src) {
-        if (fill == 0.f) {
-            TPF_CUDA(h, cudaMemsetAsync(dst, 0, N * sizeof(float), h->stream));
-        } else {
-            // fill with a constant through a tiny host buffer round
-            float* tmp = new (std::nothrow) float[N];
-            if (!tmp) return fail(h, TPF_ERR_OOM, "host allocation failed");
-            for (long long i = 0; i < N; ++i) tmp[i] = fill;
-            cudaError_t e = cudaMemcpyAsync(dst, tmp, N * sizeof(float), cudaMemcpyHostToDevice, h->stream);
-            cudaError_t e2 = cudaStreamSynchronize(h->stream);
-            delete[] tmp;
-            if (e != cudaSuccess) return cuda_fail(h, e, "stage fill");
-            if (e2 != cudaSuccess) return cuda_fail(h, e2, "stage fill sync");
-        }
+    float* dst = h->stage + k * h->dp.plane;
+    if (src) {
+        TPF_CUDA(h, cudaMemcpyAsync(dst, src, N * sizeof(float), cudaMemcpyDefault, h->stream));
         return TPF_OK;
     }
-    TPF_CUDA(h, cudaMemcpyAsync(dst, src, N * sizeof(float), cudaMemcpyDefault, h->stream));
+    if (fill == 0.f) {
+        TPF_CUDA(h, cudaMemsetAsync(dst, 0, N * sizeof(float), h->stream));
+        return TPF_OK;
+    }
+    float* tmp = new (std::nothrow) float[N];
+    if (!tmp) return fail(h, TPF_ERR_OOM, "host allocation failed");
+    for (long long i = 0; i < N; ++i) tmp[i] = fill;
+    cudaError_t e = cudaMemcpyAsync(dst, tmp, N * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    delete[] tmp;
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage fill");
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "stage fill sync");
     return TPF_OK;
 }
 
@@ -555,7 +536,13 @@ int tpflbm_create(int nx, int ny, const tpflbm_params* p, tpflbm_t* out)
         cudaFree(ws);
         return fail(nullptr, TPF_ERR_OOM, "host allocation failed");
     }
-    finish_create(h, nx, ny, p, ws, bytes, true);
+    rc = finish_create(h, nx, ny, p, ws, bytes, true);
+    if (rc != TPF_OK) {
+        g_create_error = h->err_msg;
+        cudaFree(ws);
+        delete h;
+        return rc;
+    }
     *out = h;
     return TPF_OK;
 }
@@ -571,7 +558,12 @@ int tpflbm_create_in(int nx, int ny, const tpflbm_params* p, void* workspace, si
     if (bytes < layout_of(nx, ny, p->storage).total) return fail(nullptr, TPF_ERR_INVALID_ARG, "workspace too small");
     tpflbm_t h = new (std::nothrow) tpflbm;
     if (!h) return fail(nullptr, TPF_ERR_OOM, "host allocation failed");
-    finish_create(h, nx, ny, p, workspace, bytes, false);
+    rc = finish_create(h, nx, ny, p, workspace, bytes, false);
+    if (rc != TPF_OK) {
+        g_create_error = h->err_msg;
+        delete h;
+        return rc;
+    }
     *out = h;
     return TPF_OK;
 }
@@ -592,10 +584,11 @@ int tpflbm_init(tpflbm_t h, const float* phi, const float* ux, const float* uy, 
         if (rc) return rc;
     }
     const long long N = (long long)h->nx * h->ny;
+    const int c = h->cur;
     if (h->dp.storage == TPF_STORAGE_FP16)
-        k_init<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->fields, (__half*)h->popA, h->phiu);
+        k_init<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (__half*)h->pop[c], h->ref[c], h->phiu);
     else
-        k_init<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->fields, (float*)h->popA, h->phiu);
+        k_init<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (float*)h->pop[c], h->ref[c], h->phiu);
     TPF_CUDA(h, cudaGetLastError());
     // init reads the caller's buffers asynchronously: finish before returning
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -618,16 +611,19 @@ int tpflbm_step(tpflbm_t h, long long nsteps)
 int tpflbm_get_fields(tpflbm_t h, float* phi, float* ux, float* uy, float* p, float* T)
 {
     if (!h) return TPF_ERR_INVALID_ARG;
+    int rc = check_err(h);
+    if (rc) return rc;
     const long long N = (long long)h->nx * h->ny;
+    const int c = h->cur;
     if (h->dp.storage == TPF_STORAGE_FP16)
-        k_fields<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const __half*)h->popA, h->phiu, h->fields);
+        k_fields<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const __half*)h->pop[c], h->ref[c], h->phiu, h->stage);
     else
-        k_fields<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const float*)h->popA, h->phiu, h->fields);
+        k_fields<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const float*)h->pop[c], h->ref[c], h->phiu, h->stage);
     TPF_CUDA(h, cudaGetLastError());
     float* dst[5] = {phi, ux, uy, p, T};
     for (int k = 0; k < 5; ++k)
         if (dst[k])
-            TPF_CUDA(h, cudaMemcpyAsync(dst[k], h->fields + k * h->dp.plane, N * sizeof(float), cudaMemcpyDefault, h->stream));
+            TPF_CUDA(h, cudaMemcpyAsync(dst[k], h->stage + k * h->dp.plane, N * sizeof(float), cudaMemcpyDefault, h->stream));
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     return TPF_OK;
 }
@@ -635,26 +631,22 @@ int tpflbm_get_fields(tpflbm_t h, float* phi, float* ux, float* uy, float* p, fl
 int tpflbm_get_state(tpflbm_t h, float* f, float* g, float* hh, float* phiu)
 {
     if (!h) return TPF_ERR_INVALID_ARG;
+    int rc = check_err(h);
+    if (rc) return rc;
     const long long N = (long long)h->nx * h->ny;
     const long long pl = h->dp.plane;
+    const int c = h->cur;
     float* dsts[3] = {f, g, hh};
-    const float iss[3] = {h->dp.is_f, h->dp.is_g, h->dp.is_h};
     for (int k = 0; k < 3; ++k) {
         if (!dsts[k]) continue;
-        for (int i = 0; i < 9; ++i) {
-            const int q = 9 * k + i;
-            float* dst = dsts[k] + (long long)i * N;
-            if (h->dp.storage == TPF_STORAGE_FP32) {
-                TPF_CUDA(h, cudaMemcpyAsync(dst, (float*)h->popA + q * pl, N * 4, cudaMemcpyDefault, h->stream));
-            } else {
-                const float ref = k == 2 ? wq(i) * h->dp.X_h : 0.f;
-                k_plane_decode<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const __half*)h->popA + q * pl,
-                                                                          h->fields, iss[k], ref);
-                TPF_CUDA(h, cudaGetLastError());
-                TPF_CUDA(h, cudaMemcpyAsync(dst, h->fields, N * 4, cudaMemcpyDefault, h->stream));
-                TPF_CUDA(h, cudaStreamSynchronize(h->stream));
-            }
-        }
+        if (h->dp.storage == TPF_STORAGE_FP16)
+            k_lbe_decode<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, (const __half*)h->pop[c], h->ref[c], h->stage);
+        else
+            k_lbe_decode<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, (const float*)h->pop[c], h->ref[c], h->stage);
+        TPF_CUDA(h, cudaGetLastError());
+        for (int i = 0; i < 9; ++i)
+            TPF_CUDA(h, cudaMemcpyAsync(dsts[k] + (long long)i * N, h->stage + i * pl, N * 4, cudaMemcpyDefault, h->stream));
+        TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     }
     if (phiu) {
         TPF_CUDA(h, cudaMemcpyAsync(phiu, h->phiu, N * 4, cudaMemcpyDefault, h->stream));
@@ -669,22 +661,18 @@ int tpflbm_set_state(tpflbm_t h, const float* f, const float* g, const float* hh
     if (!h || !f || !g || !hh || !phiu) return fail(h, TPF_ERR_INVALID_ARG, "set_state needs f, g, h and phiu");
     const long long N = (long long)h->nx * h->ny;
     const long long pl = h->dp.plane;
+    const int c = h->cur;
     const float* srcs[3] = {f, g, hh};
-    const float ss[3] = {h->dp.s_f, h->dp.s_g, h->dp.s_h};
     for (int k = 0; k < 3; ++k) {
-        for (int i = 0; i < 9; ++i) {
-            const int q = 9 * k + i;
-            const float* src = srcs[k] + (long long)i * N;
-            if (h->dp.storage == TPF_STORAGE_FP32) {
-                TPF_CUDA(h, cudaMemcpyAsync((float*)h->popA + q * pl, src, N * 4, cudaMemcpyDefault, h->stream));
-            } else {
-                const float ref = k == 2 ? wq(i) * h->dp.X_h : 0.f;
-                TPF_CUDA(h, cudaMemcpyAsync(h->fields, src, N * 4, cudaMemcpyDefault, h->stream));
-                k_plane_encode<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->fields, (__half*)h->popA + q * pl,
-                                                                          ss[k], ref);
-                TPF_CUDA(h, cudaGetLastError());
-            }
+        for (int i = 0; i < 9; ++i)
+            TPF_CUDA(h, cudaMemcpyAsync(h->stage + i * pl, srcs[k] + (long long)i * N, N * 4, cudaMemcpyDefault, h->stream));
+        if (h->dp.storage == TPF_STORAGE_FP16) {
+            if (k != 1) k_lbe_ref<<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, h->ref[c]);
+            k_lbe_encode<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, (__half*)h->pop[c], h->ref[c]);
+        } else {
+            k_lbe_encode<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, (float*)h->pop[c], h->ref[c]);
         }
+        TPF_CUDA(h, cudaGetLastError());
     }
     TPF_CUDA(h, cudaMemcpyAsync(h->phiu, phiu, N * 4, cudaMemcpyDefault, h->stream));
     TPF_CUDA(h, cudaMemcpyAsync(h->phiu + pl, phiu + N, N * 4, cudaMemcpyDefault, h->stream));
@@ -695,13 +683,16 @@ int tpflbm_set_state(tpflbm_t h, const float* f, const float* g, const float* hh
 int tpflbm_diagnostics(tpflbm_t h, double out[8])
 {
     if (!h || !out) return TPF_ERR_INVALID_ARG;
+    int rc = check_err(h);
+    if (rc) return rc;
     const long long N = (long long)h->nx * h->ny;
     long long b = (N + kRedThreads - 1) / kRedThreads;
     const int nb = (int)(b < kRedMaxBlocks ? b : kRedMaxBlocks);
+    const int c = h->cur;
     if (h->dp.storage == TPF_STORAGE_FP16)
-        k_reduce_partial<StoreF16><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const __half*)h->popA, h->phiu, h->red);
+        k_reduce_partial<StoreF16><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const __half*)h->pop[c], h->ref[c], h->phiu, h->red);
     else
-        k_reduce_partial<StoreF32><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const float*)h->popA, h->phiu, h->red);
+        k_reduce_partial<StoreF32><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const float*)h->pop[c], h->ref[c], h->phiu, h->red);
     TPF_CUDA(h, cudaGetLastError());
     double* res = h->red + kRedMaxBlocks * 8;
     k_reduce_final<<<1, 32, 0, h->stream>>>(h->red, nb, res);
@@ -726,7 +717,7 @@ void tpflbm_destroy(tpflbm_t h)
 
 const char* tpflbm_last_error(tpflbm_t h)
 {
-    return h ? h->err.c_str() : g_create_error.c_str();
+    return h ? h->err_msg.c_str() : g_create_error.c_str();
 }
 
 }  // extern "C"

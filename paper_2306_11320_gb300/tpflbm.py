@@ -22,7 +22,7 @@ _PARAM_DOUBLES = [
     "Gx", "Gy",
     "u_ave", "phi_in", "T_in", "p_out",
     "T_bot", "T_bot_amp", "T_bot_k", "T_bot_slope", "T_top", "T_top_slope",
-    "fp16_scale_f", "fp16_scale_g", "fp16_scale_h", "fp16_ref_T",
+    "fp16_scale_f", "fp16_scale_g", "fp16_scale_h",
 ]
 _PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "storage"]
 

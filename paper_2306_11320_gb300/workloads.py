@@ -208,15 +208,11 @@ def random_state(nx, ny, seed=0, bc_x=0, bc_y=0, sigma_law=0, amp_u=1e-2, contra
     return params, dict(phi=phi, ux=ux, uy=uy, p=p, T=T), dict(seed=seed)
 
 
-def fp16_scales(params, T_lo=None, T_hi=None):
-    """Scales and reference temperature of the float16 population storage for a
-    workload: X_h at the middle of its wall / inlet temperature range, powers of two
-    that keep every stored deviation well inside float16's normal range."""
-    temps = [params["T_bot"], params["T_top"], params["T_in"]]
-    lo = min(temps) if T_lo is None else T_lo
-    hi = max(temps) + abs(params["T_bot_amp"]) if T_hi is None else T_hi
-    return dict(fp16_scale_f=1.0, fp16_scale_g=1024.0, fp16_scale_h=1.0,
-                fp16_ref_T=0.5 * (lo + hi))
+def fp16_scales(params):
+    """Power-of-two scales of the float16 population storage: the stored deviations
+    from the nodes' rest equilibria (of order 1e-3 for f and g, 1e-2 for h on these
+    workloads) land well inside float16's normal range."""
+    return dict(fp16_scale_f=1024.0, fp16_scale_g=1024.0, fp16_scale_h=64.0)
 
 
 def ensemble(n=256, seed=0, nx_range=(64, 512), ny_range=(64, 256), round_to=8):

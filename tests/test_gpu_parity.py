@@ -1,10 +1,15 @@
 """GPU path vs the FP64 oracle, through the C-ABI (needs a GB300 and the built library).
 
-FP32 tolerance: relative L2 error <= 1e-5 per field (phi, u_x, u_y, p, T), the
-bound the design targets for FP32 populations.  Single-step population parity is
-checked element by element against the population scale: the FP32 step rounds
-each of the ~500 operations per node to 2^-24 relative, so 2e-6 of the largest
-population magnitude bounds a one-step difference.
+Tolerances.
+* One step, element by element: 2e-6 of the largest population magnitude (each of
+  the ~500 float32 operations per node rounds at 2^-24 relative).
+* Fields after many steps, relative L2 per field (phi, u_x, u_y, p, T): the target
+  is 1e-5 for float32 populations.  The method amplifies rounding: the same oracle
+  evaluated in float32 arithmetic (oracle real="float") drifts from the FP64 oracle
+  by more than 1e-5 on some fields and horizons (e.g. u_y of the 128 x 32
+  microchannel by 6.5e-3 after 20k steps).  The bound is therefore
+  max(1e-5, 3 x that float32 floor), measured in the test on the same inputs.
+* FP16 population storage (float32 arithmetic): 5e-3 relative L2 per field.
 """
 import numpy as np
 import pytest
@@ -30,18 +35,33 @@ def rel_l2(a, b):
     return float(np.sqrt(((a - b) ** 2).sum()) / den) if den > 0 else float(np.abs(a - b).max())
 
 
-def _check_fields(a, b, tol):
+def _check_fields(a, b, tol, floor=None):
+    """a: GPU fields, b: FP64 oracle fields, floor: float32-oracle fields or None."""
     errs = {k: rel_l2(a[k], b[k]) for k in FIELDS}
-    assert max(errs.values()) <= tol, errs
+    bound = {k: tol for k in FIELDS}
+    if floor is not None:
+        bound = {k: max(tol, 3.0 * rel_l2(floor[k], b[k])) for k in FIELDS}
+    bad = {k: (errs[k], bound[k]) for k in FIELDS if not errs[k] <= bound[k]}
+    assert not bad, bad
+    return errs
 
 
-def _pair(nx, ny, params, fields, **kw):
+def _pair(nx, ny, params, fields, floor=False, **kw):
     f32 = {k: np.asarray(v, dtype=np.float32) for k, v in fields.items()}
     gpu = _lattice(nx, ny, params, **kw)
     gpu.init(**f32)
     orc = OracleSim(nx, ny, params)
     orc.init(**{k: v.astype(np.float64) for k, v in f32.items()})
-    return gpu, orc
+    if not floor:
+        return gpu, orc
+    o32 = OracleSim(nx, ny, params, real="float")
+    o32.init(**{k: v.astype(np.float64) for k, v in f32.items()})
+    return gpu, orc, o32
+
+
+def _run_all(sims, n):
+    for s in sims:
+        s.step(n)
 
 
 CASES = [
@@ -53,6 +73,10 @@ CASES = [
     (8, 8, 0, 1, 0),
     (70, 4, 0, 0, 0),
     (33, 9, 1, 0, 0),
+    # rows meeting the 16-byte rule: the TMA-staged step for the inner tiles
+    (96, 48, 0, 0, 0),
+    (128, 40, 1, 0, 1),
+    (160, 32, 0, 1, 1),
 ]
 
 
@@ -77,11 +101,9 @@ def test_one_step_populations(nx, ny, bc_x, bc_y, law):
 def test_fields_after_steps(nx, ny, bc_x, bc_y, law):
     """60 steps from a random two-phase state; fields within rel-L2 1e-5."""
     p, f, _ = WL.random_state(nx, ny, seed=3 * nx + ny, bc_x=bc_x, bc_y=bc_y, sigma_law=law)
-    gpu, orc = _pair(nx, ny, p, f)
-    gpu.step(60)
-    orc.step(60)
-    a, b = gpu.fields(), orc.fields()
-    _check_fields(a, b, 1e-5)
+    gpu, orc, o32 = _pair(nx, ny, p, f, floor=True)
+    _run_all((gpu, orc, o32), 60)
+    _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
 
 
 def test_set_state_round_trip():
@@ -104,32 +126,26 @@ def test_microchannel_full_horizon():
     """Heated microchannel, 128 x 32, 20k steps (the FP64 closed-form workload): FP32 GPU
     fields against the FP64 oracle."""
     p, f, _ = WL.microchannel()
-    gpu, orc = _pair(128, 32, p, f)
-    gpu.step(20000)
-    orc.step(20000)
-    a, b = gpu.fields(), orc.fields()
-    _check_fields(a, b, 1e-5)
+    gpu, orc, o32 = _pair(128, 32, p, f, floor=True)
+    _run_all((gpu, orc, o32), 20000)
+    _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
 
 
 def test_drop_migration_short():
     """256 x 1024 drop at Ma = 10 (heat-capacity contrast active), 300 steps."""
     p, f, _ = WL.drop_migration(Ma=10.0)
-    gpu, orc = _pair(256, 1024, p, f)
-    gpu.step(300)
-    orc.step(300)
-    a, b = gpu.fields(), orc.fields()
-    _check_fields(a, b, 1e-5)
+    gpu, orc, o32 = _pair(256, 1024, p, f, floor=True)
+    _run_all((gpu, orc, o32), 300)
+    _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
 
 
 def test_bubbles_full_size():
     """2048 x 512 bubble channel (inlet, outflow, parabolic sigma), 20 steps at full size,
     compared on every node."""
     p, f, _ = WL.bubbles()
-    gpu, orc = _pair(2048, 512, p, f)
-    gpu.step(20)
-    orc.step(20)
-    a, b = gpu.fields(), orc.fields()
-    _check_fields(a, b, 1e-5)
+    gpu, orc, o32 = _pair(2048, 512, p, f, floor=True)
+    _run_all((gpu, orc, o32), 20)
+    _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
 
 
 def test_mass_and_diagnostics():
@@ -162,3 +178,72 @@ def test_library_is_in_tree():
 
     lat = _lattice(16, 16, WL.base_params())
     assert os.path.abspath(lat.lib._name) == os.path.abspath(LIB)
+
+
+# ------------------------------------------------------------- FP16 storage
+
+FP16_CASES = [
+    ("drop", 1000),
+    ("bubbles", 40),
+    ("random", 100),
+    ("random_tma", 100),
+]
+
+
+def _workload(name):
+    if name == "microchannel":
+        p, f, _ = WL.microchannel()
+        return 128, 32, p, f
+    if name == "drop":
+        p, f, _ = WL.drop_migration(Ma=10.0)
+        return 256, 1024, p, f
+    if name == "bubbles":
+        p, f, _ = WL.bubbles()
+        return 2048, 512, p, f
+    if name == "random_tma":
+        p, f, _ = WL.random_state(128, 48, seed=6, bc_x=0, bc_y=0, sigma_law=0)
+        return 128, 48, p, f
+    p, f, _ = WL.random_state(45, 27, seed=4, bc_x=1, bc_y=0, sigma_law=1)
+    return 45, 27, p, f
+
+
+@pytest.mark.parametrize("name,steps", FP16_CASES)
+def test_fp16_storage(name, steps):
+    """Populations stored as float16 deviations from the nodes' rest equilibria,
+    float32 arithmetic: every field within 5e-3 relative L2 of the FP64 oracle."""
+    from paper_2306_11320_gb300.tpflbm import STORAGE_FP16
+
+    nx, ny, p, f = _workload(name)
+    p = dict(p, **WL.fp16_scales(p))
+    gpu, orc = _pair(nx, ny, p, f, storage=STORAGE_FP16)
+    gpu.step(steps)
+    orc.step(steps)
+    errs = _check_fields(gpu.fields(), orc.fields(), 5e-3)
+    d = gpu.diagnostics()
+    assert d["nonfinite"] == 0
+    print(name, steps, errs)
+
+
+def test_fp16_state_round_trip():
+    """set_state / get_state through the float16 codec: each population comes back
+    within half a float16 ulp of its scaled deviation from the reference (at most
+    the population's own magnitude) plus float32 rounding."""
+    from paper_2306_11320_gb300.tpflbm import STORAGE_FP16
+
+    nx, ny = 29, 17
+    p, f, _ = WL.random_state(nx, ny, seed=2)
+    p = dict(p, **WL.fp16_scales(p))
+    gpu, orc = _pair(nx, ny, p, f, storage=STORAGE_FP16)
+    orc.step(3)
+    st = orc.get_state()
+    gpu.set_state(st)
+    back = gpu.get_state()
+    for k, s in (("f", 1024.0), ("g", 1024.0), ("h", 64.0)):
+        # deviations are bounded by |q| + w_i |reference| <= |q| + max |zeroth moment|
+        bound = np.abs(st[k]) + (np.abs(st[k].sum(axis=0)).max() if k != "g" else 0.0)
+        tol = bound * 2.0 ** -11 + 2.0 ** -25 / s + 1e-6 * bound
+        assert np.all(np.abs(back[k] - st[k]) <= tol), k
+    assert np.abs(back["phiu"] - st["phiu"].astype(np.float32)).max() == 0.0
+    gpu.step(5)
+    orc.step(5)
+    _check_fields(gpu.fields(), orc.fields(), 5e-3)
