@@ -133,6 +133,34 @@ int tpflbm_set_state(tpflbm_t h, const float *f, const float *g, const float *hh
  * U_r = out[3] / out[4] is the migration velocity of Sec. 4.2.  Synchronises. */
 int tpflbm_diagnostics(tpflbm_t h, double out[8]);
 
+/* Same eight reductions as tpflbm_diagnostics, for a state held in caller memory,
+ * allocating no device memory at all.  (The paper has no counterpart: this serves
+ * callers that cannot call cudaMalloc, such as code running inside a memory pool
+ * or allocator callback, a CUDA graph being built from pre-planned buffers, or a
+ * host that hands out only fixed buffers it owns.)
+ *   pop   device pointer, 27 population planes (f 0-8, g 9-17, h 18-26) of `plane`
+ *         elements each, [ny][nx] inside a plane; float32, or float16 encoded as in
+ *         tpflbm_params.storage when p->storage is TPF_STORAGE_FP16.
+ *   plane elements per plane, >= nx * ny.
+ *   ref   FP16 storage only: 2 float planes (phi, then T, of every node at the
+ *         previous time level) of `plane` elements; NULL for FP32.
+ *   phiu  device pointer, 2 float planes of `plane` elements ((phi u) of the
+ *         previous step).
+ *   out   8 doubles, host or device memory; same meaning as tpflbm_diagnostics.
+ *   stream cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ * The kernel's scratch (per-block partial sums) is a fixed array of 1024 x 8 + 8
+ * doubles (65,600 bytes) compiled into the library; every GPU that loads the
+ * library holds it until the process exits.  Any lattice the library accepts
+ * (nx, ny >= 3, nx * ny <= 2^30) fits, because the kernel walks the lattice with
+ * at most 1024 blocks; larger sizes and invalid arguments return
+ * TPF_ERR_INVALID_ARG (message in tpflbm_last_error(NULL)).  The first call on a
+ * device looks up that array's device address, so make it before any stream
+ * capture.  All calls share the array and each call overwrites every entry it
+ * reads, so nothing needs clearing; calls whose work overlaps on the GPU (for
+ * example on two streams) race on it and must be serialised by the caller. */
+int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params *p, const void *pop, long long plane,
+                              const float *ref, const float *phiu, double out[8], void *stream);
+
 /* Number of time steps taken since tpflbm_init. */
 long long tpflbm_time(tpflbm_t h);
 

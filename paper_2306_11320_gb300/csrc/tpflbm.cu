@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -22,6 +23,7 @@ using namespace tpf;
 namespace {
 
 constexpr int kBX = 32, kBY = 8;
+constexpr int kMaxDevices = 64;
 
 // ------------------------------------------------------- auxiliary kernels
 
@@ -208,6 +210,12 @@ __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, 
 }
 
 }  // namespace
+
+// Scratch of tpflbm_diagnostics_static: the per-block partial sums (kRedMaxBlocks x 8)
+// and the 8 results, in a fixed device array so that the entry point allocates
+// nothing.  Host code must not pass this name to a kernel (on the host it is only a
+// stand-in); it uses the address cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) double g_diag_scratch[kRedMaxBlocks * 8 + 8];
 
 // ===================================================================== host
 
@@ -700,6 +708,62 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8])
     TPF_CUDA(h, cudaMemcpyAsync(out, res, 8 * sizeof(double), cudaMemcpyDefault, h->stream));
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (out[7] > 0) return fail(h, TPF_ERR_NONFINITE, "non-finite values in the state");
+    return TPF_OK;
+}
+
+int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void* pop, long long plane,
+                              const float* ref, const float* phiu, double out[8], void* stream)
+{
+    std::string why;
+    int rc = validate(nx, ny, p, why);
+    if (rc != TPF_OK) return fail(nullptr, rc, "tpflbm_diagnostics_static: " + why);
+    if (!pop || !phiu || !out) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: pop, phiu and out are required");
+    if (plane < (long long)nx * ny) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: plane must be >= nx * ny");
+    if (plane > (1LL << 31) / 27) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: plane too large");
+    const bool f16 = p->storage == TPF_STORAGE_FP16;
+    if (f16 && !ref) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: FP16 storage needs the reference planes");
+
+    // the scratch's device address on the current device, looked up once per device
+    static std::mutex mu;
+    static double* addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, TPF_ERR_UNSUPPORTED, "tpflbm_diagnostics_static: device index out of range");
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            void* a = nullptr;
+            e = cudaGetSymbolAddress(&a, g_diag_scratch);
+            if (e != cudaSuccess)
+                return fail(nullptr, TPF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            addr[dev] = (double*)a;
+        }
+        scratch = addr[dev];
+    }
+
+    DevParams P = make_dev_params(nx, ny, *p);
+    P.plane = plane;
+    const long long N = (long long)nx * ny;
+    const long long b = (N + kRedThreads - 1) / kRedThreads;
+    const int nb = (int)(b < kRedMaxBlocks ? b : kRedMaxBlocks);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (f16)
+        k_reduce_partial<StoreF16><<<nb, kRedThreads, 0, s>>>(P, (const __half*)pop, ref, phiu, scratch);
+    else
+        k_reduce_partial<StoreF32><<<nb, kRedThreads, 0, s>>>(P, (const float*)pop, ref, phiu, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("k_reduce_partial: ") + cudaGetErrorString(e));
+    double* res = scratch + kRedMaxBlocks * 8;
+    k_reduce_final<<<1, 32, 0, s>>>(scratch, nb, res);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 8 * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("tpflbm_diagnostics_static: ") + cudaGetErrorString(e));
+    double nf = 0.0;
+    if (cudaMemcpy(&nf, res + 7, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess && nf > 0)
+        return fail(nullptr, TPF_ERR_NONFINITE, "non-finite values in the state");
     return TPF_OK;
 }
 

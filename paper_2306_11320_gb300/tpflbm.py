@@ -58,6 +58,7 @@ SIGNATURES = {
     "tpflbm_get_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_set_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_diagnostics": ([_vp, _dp], _ip),
+    "tpflbm_diagnostics_static": ([_ip, _ip, C.POINTER(Params), _vp, C.c_longlong, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_time": ([_vp], C.c_longlong),
     "tpflbm_destroy": ([_vp], None),
     "tpflbm_last_error": ([_vp], C.c_char_p),
