@@ -170,6 +170,52 @@ void tpflbm_destroy(tpflbm_t h);
 /* Message of the last failure on h (or of the last failed create when h is NULL). */
 const char *tpflbm_last_error(tpflbm_t h);
 
+/* ------------------------------------------------------------------ ensembles
+ * A batch advances n independent lattices (sizes, parameters and boundary kinds may
+ * all differ; storage must be the same) together: one persistent launch per time
+ * step walks a list of (lattice, tile) pairs and runs the same per-tile step as a
+ * single lattice (general tile path); pairs of steps are replayed from a CUDA graph.
+ * The tile shape is one of a few compiled shapes (tpflbm_batch_variants), chosen by
+ * tpflbm_batch_tune or set directly.  The library allocates every lattice's memory. */
+typedef struct tpflbm_batch *tpflbm_batch_t;
+
+/* nx[k], ny[k] (3 <= both < 65536) and params[k] of lattice k = 0..n-1.  The batch
+ * works on its own non-blocking stream until tpflbm_batch_set_stream. */
+int tpflbm_batch_create(int n, const int *nx, const int *ny, const tpflbm_params *params,
+                        tpflbm_batch_t *out);
+/* Order the batch's work on `stream` (a non-default cudaStream_t: graphs are captured on it). */
+int tpflbm_batch_set_stream(tpflbm_batch_t b, void *stream);
+/* Number of lattices. */
+int tpflbm_batch_size(tpflbm_batch_t b);
+/* The handle of lattice k (owned by the batch; valid until tpflbm_batch_destroy), for
+ * the single-lattice read-back calls (tpflbm_get_state, tpflbm_diagnostics, ...). */
+int tpflbm_batch_lattice(tpflbm_batch_t b, int k, tpflbm_t *out);
+/* tpflbm_init of lattice k (same field conventions). */
+int tpflbm_batch_init(tpflbm_batch_t b, int k, const float *phi, const float *ux, const float *uy,
+                      const float *p, const float *T);
+/* Advance every lattice by nsteps >= 0 time steps; returns after enqueueing. */
+int tpflbm_batch_step(tpflbm_batch_t b, long long nsteps);
+/* tpflbm_get_fields of lattice k. */
+int tpflbm_batch_get_fields(tpflbm_batch_t b, int k, float *phi, float *ux, float *uy, float *p, float *T);
+/* tpflbm_diagnostics of every lattice: out[8 k + j], j as in tpflbm_diagnostics. */
+int tpflbm_batch_diagnostics(tpflbm_batch_t b, double *out);
+/* The compiled tile shapes: *count of them, shape v is bx[v] x by[v] nodes (arrays of
+ * at least *count entries, or NULL). */
+int tpflbm_batch_variants(int *count, int *bx, int *by);
+/* Use tile shape v for the following steps. */
+int tpflbm_batch_set_variant(tpflbm_batch_t b, int v);
+/* Time every tile shape over `steps` (>= 2, rounded down to even) steps of the
+ * current state and keep the fastest; ms_per_step[v] (or NULL) receives each shape's
+ * time per step, *best (or NULL) the chosen shape.  The batch advances by
+ * kinds x (steps + 2) steps. */
+int tpflbm_batch_tune(tpflbm_batch_t b, int steps, double *ms_per_step, int *best);
+/* Steps taken since creation. */
+long long tpflbm_batch_time(tpflbm_batch_t b);
+/* Release the batch and every lattice in it.  NULL-safe. */
+void tpflbm_batch_destroy(tpflbm_batch_t b);
+/* Message of the last failure on b (or of the last failed create when b is NULL). */
+const char *tpflbm_batch_last_error(tpflbm_batch_t b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,408 @@
+// Batched ensemble: many independent lattices of uneven sizes and parameters
+// advanced together by one persistent step launch per time step, replayed from a
+// CUDA graph, with the tile shape chosen by timing every compiled shape.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tpflbm.h"
+#include "handle.h"
+#include "lattice.cuh"
+#include "step.cuh"
+
+using namespace tpf;
+
+namespace {
+
+// One lattice of the ensemble as the batch kernel sees it.
+struct InstDesc {
+    DevParams P;
+    void* pop[2];
+    float* ref[2];
+    float* phiu;
+};
+
+// Tile shapes the autotuner chooses from (BX x BY nodes, one thread per node).
+constexpr int kNumVariants = 4;
+constexpr int kVarBX[kNumVariants] = {32, 32, 32, 64};
+constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4};
+
+// Persistent CTAs walk the work list of (instance, tile) pairs; each tile goes
+// through the general tile routine with its instance's parameters and buffers.
+template <int BX, int BY, class S>
+__global__ void __launch_bounds__(BX * BY)
+k_step_batch(const InstDesc* __restrict__ inst, const int2* __restrict__ work, int nwork, int parity)
+{
+    __shared__ RingSmem<BX, BY> sm;
+    __shared__ DevParams P;
+    __shared__ const void* bufs[6];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int2 item = work[w];
+        if (threadIdx.x == 0) {
+            const InstDesc& d = inst[item.x];
+            P = d.P;
+            bufs[0] = d.pop[parity];
+            bufs[1] = d.pop[parity ^ 1];
+            bufs[2] = d.ref[parity];
+            bufs[3] = d.ref[parity ^ 1];
+            bufs[4] = d.phiu;
+        }
+        __syncthreads();
+        const typename S::elem* A = (const typename S::elem*)bufs[0];
+        typename S::elem* B = (typename S::elem*)bufs[1];
+        step_tile_general<BX, BY, S>(P, A, B, (float*)bufs[4], (const float*)bufs[2], (float*)bufs[3], sm,
+                                     item.y & 0xffff, item.y >> 16);
+        // step_tile_general ends with a barrier: P and bufs are free again
+    }
+}
+
+template <int V, class S>
+void launch_variant(const InstDesc* inst, const int2* work, int nwork, int parity, int grid, cudaStream_t s)
+{
+    constexpr int BX = kVarBX[V], BY = kVarBY[V];
+    k_step_batch<BX, BY, S><<<grid, BX * BY, 0, s>>>(inst, work, nwork, parity);
+}
+
+template <class S>
+void launch(int v, const InstDesc* inst, const int2* work, int nwork, int parity, int grid, cudaStream_t s)
+{
+    switch (v) {
+        case 0: launch_variant<0, S>(inst, work, nwork, parity, grid, s); break;
+        case 1: launch_variant<1, S>(inst, work, nwork, parity, grid, s); break;
+        case 2: launch_variant<2, S>(inst, work, nwork, parity, grid, s); break;
+        default: launch_variant<3, S>(inst, work, nwork, parity, grid, s); break;
+    }
+}
+
+template <int V, class S>
+int occupancy_variant()
+{
+    constexpr int BX = kVarBX[V], BY = kVarBY[V];
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<BX, BY, S>, BX * BY, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, per_sm);
+}
+
+template <class S>
+int occupancy(int v)
+{
+    switch (v) {
+        case 0: return occupancy_variant<0, S>();
+        case 1: return occupancy_variant<1, S>();
+        case 2: return occupancy_variant<2, S>();
+        default: return occupancy_variant<3, S>();
+    }
+}
+
+}  // namespace
+
+struct tpflbm_batch {
+    int n = 0;
+    int storage = 0;
+    int num_sms = 0;
+    std::vector<tpflbm_t> inst;
+    InstDesc* d_inst = nullptr;
+    int2* d_work[kNumVariants] = {};
+    int nwork[kNumVariants] = {};
+    int grid[kNumVariants] = {};
+    int variant = 1;
+    int parity = 0;
+    long long t = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph[kNumVariants][2] = {};  // two steps, starting at parity 0 / 1
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+int bfail(tpflbm_batch_t b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    else g_batch_error = msg;
+    return code;
+}
+
+#define TPF_BCUDA(b, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return bfail((b), TPF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void launch_batch(tpflbm_batch_t b, int v, int parity)
+{
+    if (b->storage == TPF_STORAGE_FP16)
+        launch<StoreF16>(v, b->d_inst, b->d_work[v], b->nwork[v], parity, b->grid[v], b->stream);
+    else
+        launch<StoreF32>(v, b->d_inst, b->d_work[v], b->nwork[v], parity, b->grid[v], b->stream);
+}
+
+void sync_instances(tpflbm_batch_t b)
+{
+    for (tpflbm_t h : b->inst) {
+        h->cur = b->parity;
+        h->t = b->t;
+    }
+}
+
+void drop_graphs(tpflbm_batch_t b)
+{
+    for (int v = 0; v < kNumVariants; ++v)
+        for (int p = 0; p < 2; ++p)
+            if (b->graph[v][p]) {
+                cudaGraphExecDestroy(b->graph[v][p]);
+                b->graph[v][p] = nullptr;
+            }
+}
+
+// two steps of variant v starting at parity p, captured once into a graph
+int graph_for(tpflbm_batch_t b, int v, int p, cudaGraphExec_t* out)
+{
+    if (!b->graph[v][p]) {
+        cudaGraph_t g = nullptr;
+        TPF_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        launch_batch(b, v, p);
+        launch_batch(b, v, p ^ 1);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess) return bfail(b, TPF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph[v][p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, TPF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    *out = b->graph[v][p];
+    return TPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params* params, tpflbm_batch_t* out)
+{
+    if (!out) return bfail(nullptr, TPF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !nx || !ny || !params) return bfail(nullptr, TPF_ERR_INVALID_ARG, "need n >= 1 lattices with sizes and parameters");
+    for (int k = 0; k < n; ++k) {
+        if (params[k].storage != params[0].storage)
+            return bfail(nullptr, TPF_ERR_INVALID_ARG, "every lattice of a batch has the same storage");
+        if (nx[k] >= 65536 || ny[k] >= 65536)
+            return bfail(nullptr, TPF_ERR_INVALID_ARG, "batch lattices must have nx, ny < 65536");
+    }
+    tpflbm_batch_t b = new (std::nothrow) tpflbm_batch;
+    if (!b) return bfail(nullptr, TPF_ERR_OOM, "host allocation failed");
+    b->n = n;
+    b->storage = params[0].storage;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<InstDesc> desc(n);
+    for (int k = 0; k < n; ++k) {
+        tpflbm_t h = nullptr;
+        int rc = tpflbm_create(nx[k], ny[k], &params[k], &h);
+        if (rc != TPF_OK) {
+            std::string why = std::string("lattice ") + std::to_string(k) + ": " + tpflbm_last_error(nullptr);
+            tpflbm_batch_destroy(b);
+            return bfail(nullptr, rc, why);
+        }
+        b->inst.push_back(h);
+        desc[k].P = h->dp;
+        desc[k].pop[0] = h->pop[0];
+        desc[k].pop[1] = h->pop[1];
+        desc[k].ref[0] = h->ref[0];
+        desc[k].ref[1] = h->ref[1];
+        desc[k].phiu = h->phiu;
+    }
+    cudaError_t e = cudaMalloc(&b->d_inst, n * sizeof(InstDesc));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice);
+    for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+        std::vector<int2> work;
+        const int BX = kVarBX[v], BY = kVarBY[v];
+        // tiles of all lattices, interleaved so that neighbouring items belong to
+        // different lattices (spreads each lattice's edge tiles over the CTAs)
+        std::vector<int> tx(n), ty(n);
+        long long total = 0;
+        for (int k = 0; k < n; ++k) {
+            tx[k] = (nx[k] + BX - 1) / BX;
+            ty[k] = (ny[k] + BY - 1) / BY;
+            total += (long long)tx[k] * ty[k];
+        }
+        work.reserve(total);
+        for (int k = 0; k < n; ++k)
+            for (int by = 0; by < ty[k]; ++by)
+                for (int bx = 0; bx < tx[k]; ++bx) work.push_back(make_int2(k, bx | (by << 16)));
+        b->nwork[v] = (int)work.size();
+        if (b->storage == TPF_STORAGE_FP16) b->grid[v] = occupancy<StoreF16>(v) * b->num_sms;
+        else b->grid[v] = occupancy<StoreF32>(v) * b->num_sms;
+        b->grid[v] = std::min(b->grid[v], b->nwork[v]);
+        e = cudaMalloc(&b->d_work[v], work.size() * sizeof(int2));
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_work[v], work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        std::string why = std::string("batch set-up: ") + cudaGetErrorString(e);
+        tpflbm_batch_destroy(b);
+        return bfail(nullptr, TPF_ERR_CUDA, why);
+    }
+    b->own_stream = true;
+    for (tpflbm_t h : b->inst) h->stream = b->stream;
+    *out = b;
+    return TPF_OK;
+}
+
+int tpflbm_batch_set_stream(tpflbm_batch_t b, void* stream)
+{
+    if (!b || !stream) return bfail(b, TPF_ERR_INVALID_ARG, "a batch needs a non-default stream (graph capture)");
+    drop_graphs(b);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    b->own_stream = false;
+    b->stream = (cudaStream_t)stream;
+    for (tpflbm_t h : b->inst) h->stream = b->stream;
+    return TPF_OK;
+}
+
+int tpflbm_batch_size(tpflbm_batch_t b) { return b ? b->n : -1; }
+
+int tpflbm_batch_lattice(tpflbm_batch_t b, int k, tpflbm_t* out)
+{
+    if (!b || !out || k < 0 || k >= b->n) return bfail(b, TPF_ERR_INVALID_ARG, "no such lattice");
+    sync_instances(b);
+    *out = b->inst[k];
+    return TPF_OK;
+}
+
+int tpflbm_batch_init(tpflbm_batch_t b, int k, const float* phi, const float* ux, const float* uy, const float* p,
+                      const float* T)
+{
+    if (!b || k < 0 || k >= b->n) return bfail(b, TPF_ERR_INVALID_ARG, "no such lattice");
+    sync_instances(b);
+    tpflbm_t h = b->inst[k];
+    int rc = tpflbm_init(h, phi, ux, uy, p, T);
+    if (rc != TPF_OK) return bfail(b, rc, tpflbm_last_error(h));
+    h->t = b->t;
+    return TPF_OK;
+}
+
+int tpflbm_batch_step(tpflbm_batch_t b, long long nsteps)
+{
+    if (!b || nsteps < 0) return bfail(b, TPF_ERR_INVALID_ARG, "nsteps must be >= 0");
+    const int v = b->variant;
+    while (nsteps >= 2) {
+        cudaGraphExec_t g = nullptr;
+        int rc = graph_for(b, v, b->parity, &g);
+        if (rc != TPF_OK) return rc;
+        TPF_BCUDA(b, cudaGraphLaunch(g, b->stream));
+        nsteps -= 2;
+        b->t += 2;
+    }
+    if (nsteps == 1) {
+        launch_batch(b, v, b->parity);
+        TPF_BCUDA(b, cudaGetLastError());
+        b->parity ^= 1;
+        b->t += 1;
+    }
+    sync_instances(b);
+    return TPF_OK;
+}
+
+int tpflbm_batch_get_fields(tpflbm_batch_t b, int k, float* phi, float* ux, float* uy, float* p, float* T)
+{
+    if (!b || k < 0 || k >= b->n) return bfail(b, TPF_ERR_INVALID_ARG, "no such lattice");
+    sync_instances(b);
+    int rc = tpflbm_get_fields(b->inst[k], phi, ux, uy, p, T);
+    return rc == TPF_OK ? rc : bfail(b, rc, tpflbm_last_error(b->inst[k]));
+}
+
+int tpflbm_batch_diagnostics(tpflbm_batch_t b, double* out)
+{
+    if (!b || !out) return bfail(b, TPF_ERR_INVALID_ARG, "out is NULL");
+    sync_instances(b);
+    int worst = TPF_OK;
+    for (int k = 0; k < b->n; ++k) {
+        int rc = tpflbm_diagnostics(b->inst[k], out + 8 * k);
+        if (rc == TPF_ERR_NONFINITE) worst = rc;
+        else if (rc != TPF_OK) return bfail(b, rc, tpflbm_last_error(b->inst[k]));
+    }
+    if (worst != TPF_OK) return bfail(b, worst, "non-finite values in some lattice");
+    return TPF_OK;
+}
+
+int tpflbm_batch_variants(int* count, int* bx, int* by)
+{
+    if (count) *count = kNumVariants;
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (bx) bx[v] = kVarBX[v];
+        if (by) by[v] = kVarBY[v];
+    }
+    return TPF_OK;
+}
+
+int tpflbm_batch_set_variant(tpflbm_batch_t b, int v)
+{
+    if (!b || v < 0 || v >= kNumVariants) return bfail(b, TPF_ERR_INVALID_ARG, "no such tile shape");
+    b->variant = v;
+    return TPF_OK;
+}
+
+int tpflbm_batch_tune(tpflbm_batch_t b, int steps, double* ms_per_step, int* best)
+{
+    if (!b || steps < 2) return bfail(b, TPF_ERR_INVALID_ARG, "tuning needs steps >= 2");
+    steps &= ~1;
+    cudaEvent_t e0, e1;
+    TPF_BCUDA(b, cudaEventCreate(&e0));
+    TPF_BCUDA(b, cudaEventCreate(&e1));
+    int arg = b->variant;
+    double bestt = 1e300;
+    for (int v = 0; v < kNumVariants; ++v) {
+        b->variant = v;
+        int rc = tpflbm_batch_step(b, 2);  // capture and warm up
+        if (rc != TPF_OK) return rc;
+        TPF_BCUDA(b, cudaEventRecord(e0, b->stream));
+        rc = tpflbm_batch_step(b, steps);
+        if (rc != TPF_OK) return rc;
+        TPF_BCUDA(b, cudaEventRecord(e1, b->stream));
+        TPF_BCUDA(b, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TPF_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / steps;
+        if (ms_per_step) ms_per_step[v] = per;
+        if (per < bestt) {
+            bestt = per;
+            arg = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->variant = arg;
+    if (best) *best = arg;
+    return TPF_OK;
+}
+
+long long tpflbm_batch_time(tpflbm_batch_t b) { return b ? b->t : -1; }
+
+void tpflbm_batch_destroy(tpflbm_batch_t b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (tpflbm_t h : b->inst) {
+        h->stream = nullptr;
+        tpflbm_destroy(h);
+    }
+    for (int v = 0; v < kNumVariants; ++v) cudaFree(b->d_work[v]);
+    cudaFree(b->d_inst);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char* tpflbm_batch_last_error(tpflbm_batch_t b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,35 @@
+// Internal definition of a lattice handle, shared by the library's translation
+// units (the single-lattice API and the batched ensemble).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/tpflbm.h"
+#include "lattice.cuh"
+#include "step.cuh"
+
+struct tpflbm {
+    int nx = 0, ny = 0;
+    tpflbm_params hp{};
+    tpf::DevParams dp{};
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool owns = false;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* pop[2] = {nullptr, nullptr};  // population buffers; pop[cur] holds time t
+    float* ref[2] = {nullptr, nullptr}; // FP16 references, paired with pop
+    int cur = 0;
+    float* phiu = nullptr;
+    float* stage = nullptr;             // 9 float planes: fields and state I/O
+    double* red = nullptr;              // per-block partials and results of the reductions
+    int* err = nullptr;                 // device error flag of the step kernels
+    // TMA step kernel
+    bool tma = false;
+    tpf::TmaMaps maps[2]{};             // maps[c]: reading pop[c]
+    int bx0 = 0, by0 = 0, ntbx = 0, ntby = 0, grid_tma = 0;
+    long long t = 0;
+    std::string err_msg;
+};

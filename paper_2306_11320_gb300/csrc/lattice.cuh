@@ -116,13 +116,15 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     const float mu = fmaf(P.mu_b, pc, P.mu_a);
     const float lam = fmaf(P.lam_b, pc, P.lam_a);
     const float rcp = fmaf(P.rcp_b, pc, P.rcp_a);
-    const float tau_g = mu * kInvCs2 / rho + 0.5f;
+    // correctly rounded reciprocals instead of divisions
+    const float inv_rho = __frcp_rn(rho);
+    const float tau_g = mu * kInvCs2 * inv_rho + 0.5f;
     const float tau_h = lam * kInvCs2 + 0.5f;
     m.rho = rho;
     m.rcp = rcp;
-    m.inv_tau_g = 1.f / tau_g;
+    m.inv_tau_g = __frcp_rn(tau_g);
     m.src_g = 1.f - 0.5f * m.inv_tau_g;
-    m.inv_tau_h = 1.f / tau_h;
+    m.inv_tau_h = __frcp_rn(tau_h);
 
     // surface tension law and its T derivative
     float sig, dsig;
@@ -154,8 +156,8 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
         my += cy(i) * g[i];
         sne0 += g[i];
     }
-    const float ux = (mx + 0.5f * Fx) / rho;
-    const float uy = (my + 0.5f * Fy) / rho;
+    const float ux = (mx + 0.5f * Fx) * inv_rho;
+    const float uy = (my + 0.5f * Fy) * inv_rho;
     const float grx = P.drho_dphi * gpx, gry = P.drho_dphi * gpy;
     const float uu = ux * ux + uy * uy;
     const float s0 = wq(0) * (-0.5f * kInvCs2 * uu);

@@ -181,7 +181,7 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
         }
         sm.phi[kown] = sf;
         sm.T[kown] = sh;
-        sm.irc[kown] = 1.f / fmaf(P.rcp_b, clamp1(sf), P.rcp_a);
+        sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
 #pragma unroll
         for (int i = 0; i < 9; ++i) sm.h[i][kown] = h[i];
     }
@@ -224,7 +224,7 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
             }
             sm.phi[k] = sf;
             sm.T[k] = sh;
-            sm.irc[k] = 1.f / fmaf(P.rcp_b, clamp1(sf), P.rcp_a);
+            sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
         } else {
             float ph, tt;
             phiT_at(P, gx, gy, get, ph, tt);
@@ -339,18 +339,34 @@ struct TmaMaps {
     CUtensorMap ref;   // FP16 references, box RW x RH x 2
 };
 
+// phi, T and 1/(rho c_p) of a TMA tile and its ring
+template <int BX, int BY>
+struct PhiSmem {
+    static constexpr int SN = (BX + 2) * (BY + 2);
+    float phi[SN];
+    float T[SN];
+    float irc[SN];
+};
+
+// CTAs per SM the TMA kernel is built for: shared memory allows 2 (FP32) or 3 (FP16)
+template <class S>
+constexpr int kTmaMinBlocks = kRef<S> ? 3 : 2;
+
 template <int BX, int BY, class S>
-__global__ void __launch_bounds__(BX * BY, 2)
+__global__ void __launch_bounds__(BX * BY, kTmaMinBlocks<S>)
 k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typename S::elem* __restrict__ A,
            typename S::elem* __restrict__ B, float* __restrict__ phiu, const float* __restrict__ refA,
            float* __restrict__ refB, int bx0, int by0, int ntbx, int ntby, int* __restrict__ err)
 {
     using L = TmaLayout<BX, BY, S>;
     using E = typename S::elem;
-    constexpr int SX = BX + 2, SN = SX * (BY + 2);
+    constexpr int SX = BX + 2;
+    constexpr int kRing = 2 * (BX + BY) + 4;
+    static_assert(2 * kRing <= BX * BY, "one thread per ring moment");
+    static_assert(sizeof(RingSmem<BX, BY>) <= 2 * L::STAGE, "edge tiles reuse the stages");
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ RingSmem<BX, BY> sm;
+    __shared__ PhiSmem<BX, BY> sm;
 
     const int ntma = ntbx * ntby;  // TMA tiles: bx in [bx0, bx0 + ntbx), by in [by0, by0 + ntby)
     const int tilesx = (P.nx + BX - 1) / BX, tilesy = (P.ny + BY - 1) / BY;
@@ -415,31 +431,50 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
             }
         };
 
-        // phi, T, 1/(rho c_p) of the tile and its ring
-        for (int k = tid; k < SN; k += BX * BY) {
-            const int lx = k % SX, ly = k / SX;
-            float sf = 0.f, sh = 0.f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                sf += decF(sF, P.is_f, 0, i, lx, ly);
-                sh += decF(sH, P.is_h, 1, i, lx, ly);
-            }
-            sm.phi[k] = sf;
-            sm.T[k] = sh;
-            sm.irc[k] = 1.f / fmaf(P.rcp_b, clamp1(sf), P.rcp_a);
-        }
-        __syncthreads();
-
+        // own node: decoded populations, phi, T, 1/(rho c_p)
         const int tx = tid % BX, ty = tid / BX;
         const int lx = tx + 1, ly = ty + 1, kown = ly * SX + lx;
         const int x = x0 + tx, y = y0 + ty;
         const int n = y * P.nx + x;
         float f[9], g[9], h[9], phin[9], Tn[9];
+        {
+            float sf = 0.f, sh = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                f[i] = decF(sF, P.is_f, 0, i, lx, ly);
+                h[i] = decF(sH, P.is_h, 1, i, lx, ly);
+                g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, 0.f);
+                sf += f[i];
+                sh += h[i];
+            }
+            sm.phi[kown] = sf;
+            sm.T[kown] = sh;
+            sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
+        }
+        // ring: 2 (BX + BY) + 4 nodes, one zeroth moment (f or h) per thread
+        if (tid < 2 * kRing) {
+            const int r = tid < kRing ? tid : tid - kRing;
+            int rx, ry;
+            if (r < SX) { rx = r; ry = 0; }
+            else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
+            else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
+            else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
+            const int k = ry * SX + rx;
+            float s = 0.f;
+            if (tid < kRing) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, 0, i, rx, ry);
+                sm.phi[k] = s;
+                sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(s), P.rcp_a));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, 1, i, rx, ry);
+                sm.T[k] = s;
+            }
+        }
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            f[i] = decF(sF, P.is_f, 0, i, lx, ly);
-            h[i] = decF(sH, P.is_h, 1, i, lx, ly);
-            g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, 0.f);
             const int k = kown + cy(i) * SX + cx(i);
             phin[i] = sm.phi[k];
             Tn[i] = sm.T[k];
@@ -476,7 +511,7 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
             const bool inner = by >= by0 && by < by0 + ntby;
             bx = (inner && idx >= bx0) ? idx + ntbx : idx;
         }
-        step_tile_general<BX, BY, S>(P, A, B, phiu, refA, refB, sm, bx, by);
+        step_tile_general<BX, BY, S>(P, A, B, phiu, refA, refB, *reinterpret_cast<RingSmem<BX, BY>*>(dsm), bx, by);
     }
 }
 

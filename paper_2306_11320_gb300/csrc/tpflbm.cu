@@ -15,6 +15,7 @@
 #include <utility>
 
 #include "../../include/tpflbm.h"
+#include "handle.h"
 #include "lattice.cuh"
 #include "step.cuh"
 
@@ -217,33 +218,6 @@ __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, 
 // stand-in); it uses the address cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) double g_diag_scratch[kRedMaxBlocks * 8 + 8];
 
-// ===================================================================== host
-
-struct tpflbm {
-    int nx = 0, ny = 0;
-    tpflbm_params hp{};
-    DevParams dp{};
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    bool owns = false;
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-    void* pop[2] = {nullptr, nullptr};  // population buffers; pop[cur] holds time t
-    float* ref[2] = {nullptr, nullptr}; // FP16 references, paired with pop
-    int cur = 0;
-    float* phiu = nullptr;
-    float* stage = nullptr;             // 9 float planes: fields and state I/O
-    double* red = nullptr;              // kRedMaxBlocks * 8 partials + 8 results
-    int* err = nullptr;                 // device error flag of the step kernels
-    // TMA step kernel
-    bool tma = false;
-    TmaMaps maps[2]{};                  // maps[c]: reading pop[c]
-    int bx0 = 0, by0 = 0, ntbx = 0, ntby = 0, grid_tma = 0;
-    long long t = 0;
-    std::string err_msg;
-};
-
 namespace {
 
 thread_local std::string g_create_error;
@@ -312,6 +286,12 @@ int validate(int nx, int ny, const tpflbm_params* p, std::string& why)
     if (!(p->rho_l > 0 && p->rho_h > 0)) { why = "densities must be positive"; return TPF_ERR_INVALID_ARG; }
     if (!(p->mu_l > 0 && p->mu_h > 0 && p->lambda_l > 0 && p->lambda_h > 0)) { why = "mu and lambda must be positive (tau > 1/2)"; return TPF_ERR_INVALID_ARG; }
     if (!(p->cp_l > 0 && p->cp_h > 0)) { why = "heat capacities must be positive"; return TPF_ERR_INVALID_ARG; }
+    // Eq. 28 weighs the destination's old population by (1 - 1/(rho c_p)); below one
+    // that weight is negative and the thermal update amplifies instead of relaxing
+    if (p->rho_l * p->cp_l < 1.0 - 1e-9 || p->rho_h * p->cp_h < 1.0 - 1e-9) {
+        why = "heat capacitance rho * c_p must be >= 1 in both phases (lattice units)";
+        return TPF_ERR_INVALID_ARG;
+    }
     if (!(p->M_phi > 0) || !(p->W > 0)) { why = "M_phi and W must be positive"; return TPF_ERR_INVALID_ARG; }
     if (p->bc_x == 1 && p->bc_y == 1) { why = "an inlet/outflow channel needs walls (bc_y = 0)"; return TPF_ERR_INVALID_ARG; }
     if (p->fp16_scale_f < 0 || p->fp16_scale_g < 0 || p->fp16_scale_h < 0) { why = "FP16 scales must be >= 0"; return TPF_ERR_INVALID_ARG; }

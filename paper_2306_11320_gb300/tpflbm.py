@@ -62,6 +62,20 @@ SIGNATURES = {
     "tpflbm_time": ([_vp], C.c_longlong),
     "tpflbm_destroy": ([_vp], None),
     "tpflbm_last_error": ([_vp], C.c_char_p),
+    "tpflbm_batch_create": ([_ip, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(Params), C.POINTER(_vp)], _ip),
+    "tpflbm_batch_set_stream": ([_vp, _vp], _ip),
+    "tpflbm_batch_size": ([_vp], _ip),
+    "tpflbm_batch_lattice": ([_vp, _ip, C.POINTER(_vp)], _ip),
+    "tpflbm_batch_init": ([_vp, _ip, _vp, _vp, _vp, _vp, _vp], _ip),
+    "tpflbm_batch_step": ([_vp, C.c_longlong], _ip),
+    "tpflbm_batch_get_fields": ([_vp, _ip, _vp, _vp, _vp, _vp, _vp], _ip),
+    "tpflbm_batch_diagnostics": ([_vp, _dp], _ip),
+    "tpflbm_batch_variants": ([C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], _ip),
+    "tpflbm_batch_set_variant": ([_vp, _ip], _ip),
+    "tpflbm_batch_tune": ([_vp, _ip, _dp, C.POINTER(C.c_int)], _ip),
+    "tpflbm_batch_time": ([_vp], C.c_longlong),
+    "tpflbm_batch_destroy": ([_vp], None),
+    "tpflbm_batch_last_error": ([_vp], C.c_char_p),
 }
 
 
@@ -213,3 +227,93 @@ class Lattice:
             self._check(rc)
         return dict(sum_phi=vals[0], sum_rcpT=vals[1], sum_T=vals[2], Ur_num=vals[3], Ur_den=vals[4],
                     ub_num=vals[5], xb_num=vals[6], nonfinite=int(vals[7]), rc=rc)
+
+
+class Batch:
+    """An ensemble of independent lattices advanced together on the GPU.
+
+    `lattices` is a list of (nx, ny, params) with a common storage.  Fields of
+    lattice k are float32 arrays of shape (ny_k, nx_k).
+    """
+
+    def __init__(self, lattices, storage: int = STORAGE_FP32, stream=None, lib=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("tpflbm needs a CUDA device; there is no CPU fallback")
+        self.torch = torch
+        self.lib = lib if lib is not None else load_library()
+        self.n = len(lattices)
+        self.sizes = [(int(nx), int(ny)) for nx, ny, _ in lattices]
+        nxa = (C.c_int * self.n)(*[s[0] for s in self.sizes])
+        nya = (C.c_int * self.n)(*[s[1] for s in self.sizes])
+        pars = (Params * self.n)(*[make_params(p, storage) for _, _, p in lattices])
+        h = C.c_void_p()
+        rc = self.lib.tpflbm_batch_create(self.n, nxa, nya, pars, C.byref(h))
+        if rc != 0:
+            raise TpfError(rc, self.lib.tpflbm_batch_last_error(None).decode())
+        self.h = h
+        self.stream = stream
+        if stream is not None:
+            self._check(self.lib.tpflbm_batch_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TpfError(rc, self.lib.tpflbm_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tpflbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, k, phi=None, ux=None, uy=None, p=None, T=None):
+        nx, ny = self.sizes[k]
+        arrs = [None if a is None else np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float32), (ny, nx)))
+                for a in (phi, ux, uy, p, T)]
+        self._check(self.lib.tpflbm_batch_init(self.h, int(k), *[_ptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.tpflbm_batch_step(self.h, int(n)))
+
+    @property
+    def t(self) -> int:
+        return int(self.lib.tpflbm_batch_time(self.h))
+
+    def fields(self, k):
+        nx, ny = self.sizes[k]
+        out = [np.empty((ny, nx), dtype=np.float32) for _ in range(5)]
+        self._check(self.lib.tpflbm_batch_get_fields(self.h, int(k), *[_ptr(a) for a in out]))
+        return dict(zip(("phi", "ux", "uy", "p", "T"), out))
+
+    def diagnostics(self):
+        out = (C.c_double * (8 * self.n))()
+        rc = self.lib.tpflbm_batch_diagnostics(self.h, out)
+        if rc not in (0, -4):
+            self._check(rc)
+        return np.array(out[:]).reshape(self.n, 8), rc
+
+    @staticmethod
+    def variants(lib=None):
+        lib = lib if lib is not None else load_library()
+        cnt = C.c_int()
+        lib.tpflbm_batch_variants(C.byref(cnt), None, None)
+        bx = (C.c_int * cnt.value)()
+        by = (C.c_int * cnt.value)()
+        lib.tpflbm_batch_variants(C.byref(cnt), bx, by)
+        return list(zip(bx[:], by[:]))
+
+    def set_variant(self, v: int):
+        self._check(self.lib.tpflbm_batch_set_variant(self.h, int(v)))
+
+    def tune(self, steps: int = 20):
+        nv = len(self.variants(self.lib))
+        ms = (C.c_double * nv)()
+        best = C.c_int()
+        self._check(self.lib.tpflbm_batch_tune(self.h, int(steps), ms, C.byref(best)))
+        return best.value, list(ms[:])

@@ -90,7 +90,7 @@ def microchannel(nx=128, ny=32, lam_r=0.5, W=DEFAULT_W, k=1, h_frac=0.5,
 # ----------------------------------------------------------------------- drop
 
 def drop_migration(nx=256, ny=1024, R=32.0, Ma=0.1, Re=0.1, Ca=0.08, ratio=0.5,
-                   gradT=0.1, T_c=16.0, mu_h=0.2, rho_h=1.0, lambda_h=0.2, W=DEFAULT_W,
+                   gradT=0.1, T_c=16.0, mu_h=0.2, rho_h=1.0, lambda_h=None, W=DEFAULT_W,
                    M_phi=DEFAULT_M_PHI):
     """Thermocapillary drop migration in a channel with a vertical T gradient (Sec. 4.2).
 
@@ -98,11 +98,16 @@ def drop_migration(nx=256, ny=1024, R=32.0, Ma=0.1, Re=0.1, Ca=0.08, ratio=0.5,
     `ratio` to the matrix; density ratio 1.  The characteristic length is R and the
     velocity U = -sigma_T grad T R / mu_h (below Eq. 60); Re, Ma, Ca of Eq. 46 fix
     U, c_p,h, sigma_T and sigma_ref.  sigma(T_ref) = sigma_ref at the drop centre.
+    lambda_h defaults to the larger of 0.2 and the value that makes the drop's heat
+    capacitance rho c_p equal to one: the update of Eq. 28 weighs the old population
+    by (1 - 1/(rho c_p)), which turns negative (and the scheme unstable) below one.
     """
     nu_h = mu_h / rho_h
     U = Re * nu_h / R
     sigma_T = -U * mu_h / (R * gradT)
     sigma_ref = U * mu_h / Ca
+    if lambda_h is None:
+        lambda_h = max(0.2, rho_h * R * U / (Ma * min(1.0, ratio)))
     cp_h = Ma * lambda_h / (rho_h * R * U)
     xc, yc = 0.5 * (nx - 1), 0.5 * (ny - 1)
     T_at_centre = T_c + gradT * (yc + 0.5)
@@ -237,10 +242,13 @@ def ensemble(n=256, seed=0, nx_range=(64, 512), ny_range=(64, 256), round_to=8):
         if k % 2 == 0:
             p, f, m = microchannel(nx=nx, ny=ny, lam_r=lam_r)
             p["mu_l"] = mu_r * p["mu_h"]
-            # Ma = rho_h c_p,h L U / lambda_h with L = nx and U from the wall forcing
+            # Ma = rho_h c_p,h L U / lambda_h with L = nx and U from the wall forcing;
+            # rho c_p >= 1 (see drop_migration), lambda raised to keep Ma where needed
             U = abs(p["sigma_T"]) * 4.0 / nx * (ny // 2) / p["mu_h"]
-            cp = Ma * p["lambda_h"] / (nx * U)
+            cp = max(1.0, Ma * p["lambda_h"] / (nx * U))
             p["cp_h"] = p["cp_l"] = cp
+            p["lambda_h"] = cp * nx * U / Ma
+            p["lambda_l"] = lam_r * p["lambda_h"]
         else:
             R = max(6.0, 0.2 * min(nx, ny))
             p, f, m = drop_migration(nx=nx, ny=ny, R=R, Ma=Ma, ratio=1.0, gradT=0.02)

@@ -59,3 +59,8 @@ def test_workspace_size_rejects_bad_sizes():
     assert lib.tpflbm_workspace_bytes(64, 64, C.byref(p16)) < n
     bad = make_params(WL.base_params(mu_l=-1.0))
     assert lib.tpflbm_workspace_bytes(64, 64, C.byref(bad)) == 0
+    # rho c_p < 1 makes the weight (1 - 1/(rho c_p)) of Eq. 28 negative: rejected
+    low = make_params(WL.base_params(rho_l=0.5, cp_l=1.0))
+    assert lib.tpflbm_workspace_bytes(64, 64, C.byref(low)) == 0
+    ok = make_params(WL.base_params(rho_l=0.5, cp_l=2.0))
+    assert lib.tpflbm_workspace_bytes(64, 64, C.byref(ok)) > 0

@@ -1,0 +1,110 @@
+"""Batched ensemble through the C-ABI (needs a GB300): uneven lattices with their own
+parameters and boundary kinds, advanced by one persistent launch per step and
+replayed from CUDA graphs, against the FP64 oracle lattice by lattice."""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim
+from paper_2306_11320_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "ux", "uy", "p", "T")
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.sqrt((b ** 2).sum())
+    return float(np.sqrt(((a - b) ** 2).sum()) / den) if den > 0 else float(np.abs(a - b).max())
+
+
+def _members():
+    """A small ensemble: sweep instances (microchannel / drop, Ma, viscosity and
+    conductivity ratios) plus random two-phase states with every boundary kind."""
+    out = [(m["nx"], m["ny"], p, f) for p, f, m in WL.ensemble(n=6, seed=3, nx_range=(32, 96),
+                                                               ny_range=(24, 64))]
+    for (nx, ny, bx, by, law, seed) in ((41, 19, 1, 0, 1, 1), (64, 32, 0, 1, 0, 2), (37, 23, 0, 0, 1, 3)):
+        p, f, _ = WL.random_state(nx, ny, seed=seed, bc_x=bx, bc_y=by, sigma_law=law)
+        out.append((nx, ny, p, f))
+    return out
+
+
+def _batch(members, storage=0):
+    from paper_2306_11320_gb300.tpflbm import Batch
+
+    b = Batch([(nx, ny, p) for nx, ny, p, _ in members], storage=storage)
+    for k, (_, _, _, f) in enumerate(members):
+        b.init(k, **{n: v.astype(np.float32) for n, v in f.items()})
+    return b
+
+
+def test_batch_matches_oracle():
+    members = _members()
+    b = _batch(members)
+    steps = 40
+    b.step(steps)
+    for k, (nx, ny, p, f) in enumerate(members):
+        f32 = {n: v.astype(np.float32).astype(np.float64) for n, v in f.items()}
+        o = OracleSim(nx, ny, p)
+        o.init(**f32)
+        o.step(steps)
+        o32 = OracleSim(nx, ny, p, real="float")
+        o32.init(**f32)
+        o32.step(steps)
+        a, ref, fl = b.fields(k), o.fields(), o32.fields()
+        for n in FIELDS:
+            bound = max(1e-5, 3.0 * rel_l2(fl[n], ref[n]))
+            assert rel_l2(a[n], ref[n]) <= bound, (k, n, rel_l2(a[n], ref[n]), bound)
+    d, rc = b.diagnostics()
+    assert rc == 0 and d.shape == (len(members), 8) and np.all(d[:, 7] == 0)
+
+
+def test_graph_replay_equals_direct_launches():
+    members = _members()
+    b1, b2 = _batch(members), _batch(members)
+    b1.step(30)          # 15 graph replays of two steps
+    for _ in range(30):  # 30 direct launches
+        b2.step(1)
+    assert b1.t == b2.t == 30
+    for k in range(len(members)):
+        a, c = b1.fields(k), b2.fields(k)
+        for n in FIELDS:
+            assert np.array_equal(a[n], c[n]), (k, n)
+
+
+def test_tile_shapes_agree_and_tuner_picks_one():
+    from paper_2306_11320_gb300.tpflbm import Batch
+
+    members = _members()
+    shapes = Batch.variants()
+    assert len(shapes) >= 2
+    results = []
+    for v in range(len(shapes)):
+        b = _batch(members)
+        b.set_variant(v)
+        b.step(20)
+        results.append([b.fields(k) for k in range(len(members))])
+    for v in range(1, len(shapes)):
+        for k in range(len(members)):
+            for n in FIELDS:
+                assert rel_l2(results[v][k][n], results[0][k][n]) <= 1e-6, (v, k, n)
+    b = _batch(members)
+    best, ms = b.tune(steps=10)
+    assert 0 <= best < len(shapes) and all(t > 0 for t in ms)
+    assert ms[best] == min(ms)
+    assert b.t == len(shapes) * 12
+
+
+def test_fp16_batch():
+    members = [m for m in _members()]
+    members = [(nx, ny, dict(p, **WL.fp16_scales(p)), f) for nx, ny, p, f in members]
+    b = _batch(members, storage=1)
+    b.step(60)
+    for k, (nx, ny, p, f) in enumerate(members):
+        o = OracleSim(nx, ny, p)
+        o.init(**{n: v.astype(np.float32).astype(np.float64) for n, v in f.items()})
+        o.step(60)
+        a, ref = b.fields(k), o.fields()
+        for n in FIELDS:
+            assert rel_l2(a[n], ref[n]) <= 5e-3, (k, n, rel_l2(a[n], ref[n]))
