@@ -1,0 +1,521 @@
+// Training and inference kernels of the warm-start U-Net (no counterpart in the
+// paper): 3x3 convolutions as implicit GEMMs on the tensor cores (BF16 operands,
+// FP32 accumulation, mma.sync m16n8k16), their data and weight gradients, pooling,
+// upsampling, channel concatenation, the 1x1 head, the MSE loss and Adam.
+// Activations are NHWC bfloat16 with channel counts that are multiples of 32;
+// 3x3 weights are [9][Cout][Cin] (tap = (dh + 1) * 3 + (dw + 1)).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tpflbm.h"
+#include "../../include/tpfnet.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kBM = 64;  // output pixels per CTA (one row segment)
+constexpr int kKC = 32;  // input channels per K chunk
+constexpr int kPad = 8;  // smem row padding (bf16) against bank conflicts
+
+__device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// y[n, h, w, co] = act(b[co] + sum_tap sum_ci x[n, h+dh, w+dw, ci] W[tap][co][ci]).
+// CTA: 64 pixels of one image row x BN output channels; 4 warps, 16 pixels each.
+template <int BN>
+__global__ void __launch_bounds__(128)
+k_conv3x3(const bf16* __restrict__ x, int N, int H, int W, int Cin, const bf16* __restrict__ wt,
+          const float* __restrict__ bias, int Cout, int relu, bf16* __restrict__ y)
+{
+    __shared__ __align__(16) bf16 As[kBM][kKC + kPad];
+    __shared__ __align__(16) bf16 Bs[BN][kKC + kPad];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tig = lane & 3;
+    const int wblocks = (W + kBM - 1) / kBM;
+    const int row = blockIdx.x / wblocks, w0 = (blockIdx.x % wblocks) * kBM;
+    const int n = row / H, h = row % H;
+    const int co0 = blockIdx.y * BN;
+    constexpr int NT = BN / 8;
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dh = tap / 3 - 1, dw = tap % 3 - 1;
+        const int hh = h + dh;
+        for (int c0 = 0; c0 < Cin; c0 += kKC) {
+            // A: 64 pixels x 32 channels (4 x 16-byte pieces per pixel)
+            for (int k = tid; k < kBM * 4; k += 128) {
+                const int m = k >> 2, q = k & 3;
+                const int ww = w0 + m + dw;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (hh >= 0 && hh < H && ww >= 0 && ww < W)
+                    v = *reinterpret_cast<const uint4*>(x + (((size_t)n * H + hh) * W + ww) * Cin + c0 + q * 8);
+                *reinterpret_cast<uint4*>(&As[m][q * 8]) = v;
+            }
+            // B: BN output channels x 32 input channels
+            for (int k = tid; k < BN * 4; k += 128) {
+                const int co = k >> 2, q = k & 3;
+                *reinterpret_cast<uint4*>(&Bs[co][q * 8]) =
+                    *reinterpret_cast<const uint4*>(wt + ((size_t)tap * Cout + co0 + co) * Cin + c0 + q * 8);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int ks = 0; ks < kKC; ks += 16) {
+                uint32_t a[4];
+                const int r0 = warp * 16 + g;
+                a[0] = ld_pair(&As[r0][ks + 2 * tig]);
+                a[1] = ld_pair(&As[r0 + 8][ks + 2 * tig]);
+                a[2] = ld_pair(&As[r0][ks + 2 * tig + 8]);
+                a[3] = ld_pair(&As[r0 + 8][ks + 2 * tig + 8]);
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    uint32_t b[2];
+                    b[0] = ld_pair(&Bs[j * 8 + g][ks + 2 * tig]);
+                    b[1] = ld_pair(&Bs[j * 8 + g][ks + 2 * tig + 8]);
+                    mma_bf16(acc[j], a, b);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // epilogue: bias, optional ReLU, bf16 store
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int m = warp * 16 + g + 8 * r;
+            const int ww = w0 + m;
+            if (ww >= W) continue;
+            const int co = co0 + j * 8 + 2 * tig;
+            float v0 = acc[j][2 * r] + (bias ? bias[co] : 0.f);
+            float v1 = acc[j][2 * r + 1] + (bias ? bias[co + 1] : 0.f);
+            if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            __nv_bfloat162 o;
+            o.x = __float2bfloat16_rn(v0);
+            o.y = __float2bfloat16_rn(v1);
+            *reinterpret_cast<__nv_bfloat162*>(y + (((size_t)n * H + h) * W + ww) * Cout + co) = o;
+        }
+    }
+}
+
+// dW[tap][co][ci] += sum_p dz[p][co] x[p + off(tap)][ci], db[co] += sum_p dz[p][co].
+// CTA: one tap, WM co x 32 ci, a chunk of 32 pixels at a time over its pixel range;
+// accumulates in FP32 and adds into dW with atomics.  4 warps: WM/16 row blocks of
+// 16 output channels times 64/WM groups of n-tiles.
+constexpr int kWN = 32, kWK = 32;
+template <int WM>
+__global__ void __launch_bounds__(128)
+k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dz, int N, int H, int W, int Cin, int Cout,
+                int pix_per_cta, float* __restrict__ dw, float* __restrict__ db)
+{
+    constexpr int RB = WM / 16;        // row blocks
+    constexpr int NG = 4 / RB;         // n-tile groups
+    constexpr int NTW = 4 / NG;        // n-tiles (of 8 ci) per warp
+    __shared__ __align__(16) bf16 Az[WM][kWK + kPad];   // [co][p]
+    __shared__ __align__(16) bf16 Bx[kWN][kWK + kPad];  // [ci][p]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tig = lane & 3;
+    const int rb = warp % RB, ng = warp / RB;
+    const int tap = blockIdx.z % 9, split = blockIdx.z / 9;
+    const int dh = tap / 3 - 1, dwd = tap % 3 - 1;
+    const int co0 = blockIdx.y * WM, ci0 = blockIdx.x * kWN;
+    const long long P = (long long)N * H * W;
+    const long long p_begin = (long long)split * pix_per_cta;
+    const long long p_end = p_begin + pix_per_cta < P ? p_begin + pix_per_cta : P;
+    float acc[NTW][4];
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    float bacc = 0.f;
+    const bool do_bias = db && tap == 4 && blockIdx.x == 0;
+
+    for (long long p0 = p_begin; p0 < p_end; p0 += kWK) {
+        // dz tile: 32 pixels x WM co -> Az[co][p]
+        for (int k = tid; k < kWK * WM; k += 128) {
+            const int pl = k / WM, co = k % WM;
+            const long long p = p0 + pl;
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (p < p_end) v = dz[p * Cout + co0 + co];
+            Az[co][pl] = v;
+        }
+        // x tile at the tap offset: 32 pixels x 32 ci -> Bx[ci][p]
+        for (int k = tid; k < kWK * kWN; k += 128) {
+            const int pl = k / kWN, ci = k % kWN;
+            const long long p = p0 + pl;
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (p < p_end) {
+                const int w = (int)(p % W), hrow = (int)((p / W) % H), nn = (int)(p / ((long long)W * H));
+                const int hh = hrow + dh, ww = w + dwd;
+                if (hh >= 0 && hh < H && ww >= 0 && ww < W) v = x[(((long long)nn * H + hh) * W + ww) * Cin + ci0 + ci];
+            }
+            Bx[ci][pl] = v;
+        }
+        __syncthreads();
+        if (do_bias && tid < WM) {
+            for (int pl = 0; pl < kWK; ++pl) bacc += __bfloat162float(Az[tid][pl]);
+        }
+#pragma unroll
+        for (int ks = 0; ks < kWK; ks += 16) {
+            uint32_t a[4];
+            const int r0 = rb * 16 + g;
+            a[0] = ld_pair(&Az[r0][ks + 2 * tig]);
+            a[1] = ld_pair(&Az[r0 + 8][ks + 2 * tig]);
+            a[2] = ld_pair(&Az[r0][ks + 2 * tig + 8]);
+            a[3] = ld_pair(&Az[r0 + 8][ks + 2 * tig + 8]);
+#pragma unroll
+            for (int j = 0; j < NTW; ++j) {
+                const int nt = ng * NTW + j;
+                uint32_t b[2];
+                b[0] = ld_pair(&Bx[nt * 8 + g][ks + 2 * tig]);
+                b[1] = ld_pair(&Bx[nt * 8 + g][ks + 2 * tig + 8]);
+                mma_bf16(acc[j], a, b);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int co = co0 + rb * 16 + g + 8 * r;
+            const int ci = ci0 + (ng * NTW + j) * 8 + 2 * tig;
+            float* dst = dw + ((size_t)tap * Cout + co) * Cin + ci;
+            atomicAdd(dst, acc[j][2 * r]);
+            atomicAdd(dst + 1, acc[j][2 * r + 1]);
+        }
+    }
+    if (do_bias && tid < WM) atomicAdd(db + co0 + tid, bacc);
+}
+
+// flipped transpose for the data gradient: wd[tap][ci][co] = w[8 - tap][co][ci]
+__global__ void k_flip_weights(const bf16* __restrict__ w, int Cin, int Cout, bf16* __restrict__ wd)
+{
+    const long long total = 9LL * Cin * Cout;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(k % Cout);
+        const long long r = k / Cout;
+        const int ci = (int)(r % Cin), tap = (int)(r / Cin);
+        wd[k] = w[((size_t)(8 - tap) * Cout + co) * Cin + ci];
+    }
+}
+
+__global__ void k_relu_mask(bf16* __restrict__ d, const bf16* __restrict__ y, long long count)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(y[k]) > 0.f)) d[k] = __float2bfloat16_rn(0.f);
+}
+
+// 2x2 average pooling and its adjoint; nearest upsampling and its adjoint
+__global__ void k_pool(const bf16* __restrict__ x, int N, int H, int W, int C, bf16* __restrict__ y)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)N * Ho * Wo * C;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        long long r = k / C;
+        const int wo = (int)(r % Wo); r /= Wo;
+        const int ho = (int)(r % Ho);
+        const int n = (int)(r / Ho);
+        const size_t b = (((size_t)n * H + 2 * ho) * W + 2 * wo) * C + c;
+        const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (size_t)W * C]) +
+                        __bfloat162float(x[b + (size_t)W * C + C]);
+        y[k] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+// dx[fine] (+)= dy[coarse] / 4
+__global__ void k_pool_back(const bf16* __restrict__ dy, int N, int H, int W, int C, bf16* __restrict__ dx, int accumulate)
+{
+    const long long total = (long long)N * H * W * C;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        long long r = k / C;
+        const int w = (int)(r % W); r /= W;
+        const int hh = (int)(r % H);
+        const int n = (int)(r / H);
+        float v = 0.25f * __bfloat162float(dy[(((size_t)n * (H / 2) + hh / 2) * (W / 2) + w / 2) * C + c]);
+        if (accumulate) v += __bfloat162float(dx[k]);
+        dx[k] = __float2bfloat16_rn(v);
+    }
+}
+// y[n, h, w, cofs + c] = x[n, h/2, w/2, c] : upsampled x into channels [cofs, cofs + C) of a Ctot tensor
+__global__ void k_up_into(const bf16* __restrict__ x, int N, int H, int W, int C, bf16* __restrict__ y, int Ctot, int cofs)
+{
+    const long long total = (long long)N * H * W * C;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        long long r = k / C;
+        const int w = (int)(r % W); r /= W;
+        const int hh = (int)(r % H);
+        const int n = (int)(r / H);
+        y[(((size_t)n * H + hh) * W + w) * Ctot + cofs + c] = x[(((size_t)n * (H / 2) + hh / 2) * (W / 2) + w / 2) * C + c];
+    }
+}
+// dx[coarse] = sum of the 4 fine dy values in channels [cofs, cofs + C) of a Ctot tensor
+__global__ void k_up_back(const bf16* __restrict__ dy, int N, int H, int W, int Ctot, int cofs, int C, bf16* __restrict__ dx)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long long total = (long long)N * Ho * Wo * C;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        long long r = k / C;
+        const int wo = (int)(r % Wo); r /= Wo;
+        const int ho = (int)(r % Ho);
+        const int n = (int)(r / Ho);
+        const size_t b = (((size_t)n * H + 2 * ho) * W + 2 * wo) * Ctot + cofs + c;
+        const float s = __bfloat162float(dy[b]) + __bfloat162float(dy[b + Ctot]) +
+                        __bfloat162float(dy[b + (size_t)W * Ctot]) + __bfloat162float(dy[b + (size_t)W * Ctot + Ctot]);
+        dx[k] = __float2bfloat16_rn(s);
+    }
+}
+// copy channels [sofs, sofs + C) of an Sc-channel tensor into channels [dofs, dofs + C) of a Dc-channel
+// tensor (concatenation and its adjoint split); accumulate adds into the destination
+__global__ void k_channels(const bf16* __restrict__ src, int Sc, int sofs, long long pixels, int C, bf16* __restrict__ dst,
+                           int Dc, int dofs, int accumulate)
+{
+    const long long total = pixels * C;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        const long long p = k / C;
+        float v = __bfloat162float(src[p * Sc + sofs + c]);
+        bf16* d = dst + p * Dc + dofs + c;
+        if (accumulate) v += __bfloat162float(*d);
+        *d = __float2bfloat16_rn(v);
+    }
+}
+
+// 1x1 head: out[p][o] = b[o] + sum_c x[p][c] W[c][o] (FP32 weights and output)
+__global__ void k_head(const bf16* __restrict__ x, long long pixels, int C, const float* __restrict__ Wt,
+                       const float* __restrict__ b, int Cout, float* __restrict__ out)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pixels * Cout; k += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(k % Cout);
+        const long long p = k / Cout;
+        float s = b[o];
+        for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(x[p * C + c]), Wt[c * Cout + o], s);
+        out[k] = s;
+    }
+}
+// head gradients: dx[p][c] = sum_o dout[p][o] W[c][o]; dW[c][o] += sum_p x[p][c] dout[p][o]; db[o] += sum_p dout[p][o]
+__global__ void k_head_back(const bf16* __restrict__ x, const float* __restrict__ dout, long long pixels, int C,
+                            const float* __restrict__ Wt, int Cout, bf16* __restrict__ dx, float* __restrict__ dW,
+                            float* __restrict__ db)
+{
+    extern __shared__ float sh[];  // C * Cout + Cout partial sums
+    for (int k = threadIdx.x; k < C * Cout + Cout; k += blockDim.x) sh[k] = 0.f;
+    __syncthreads();
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < pixels; p += (long long)gridDim.x * blockDim.x) {
+        for (int c = 0; c < C; ++c) {
+            float s = 0.f;
+            const float xv = __bfloat162float(x[p * C + c]);
+            for (int o = 0; o < Cout; ++o) {
+                const float d = dout[p * Cout + o];
+                s = fmaf(d, Wt[c * Cout + o], s);
+                atomicAdd(&sh[c * Cout + o], xv * d);
+            }
+            dx[p * C + c] = __float2bfloat16_rn(s);
+        }
+        for (int o = 0; o < Cout; ++o) atomicAdd(&sh[C * Cout + o], dout[p * Cout + o]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C * Cout; k += blockDim.x) atomicAdd(&dW[k], sh[k]);
+    for (int k = threadIdx.x; k < Cout; k += blockDim.x) atomicAdd(&db[k], sh[C * Cout + k]);
+}
+
+// mean squared error with channel weights; grad = d loss / d pred; loss accumulated in FP64
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, const float* __restrict__ wch,
+                      long long count, int C, float* __restrict__ grad, double* __restrict__ loss)
+{
+    double acc = 0.0;
+    const float inv = 1.f / (float)count;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x) {
+        const float wc = wch ? wch[k % C] : 1.f;
+        const float d = pred[k] - target[k];
+        acc += (double)d * d * wc;
+        if (grad) grad[k] = 2.f * d * wc * inv;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)count);
+}
+
+// Adam on FP32 master weights, refreshing the bf16 copy used by the convolutions
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m, float* __restrict__ v,
+                       long long count, float lr, float b1, float b2, float eps, float c1, float c2,
+                       bf16* __restrict__ pb)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x) {
+        const float gk = gr[k];
+        const float mk = b1 * m[k] + (1.f - b1) * gk;
+        const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        const float pk = p[k] - lr * (mk * c1) / (sqrtf(vk * c2) + eps);
+        p[k] = pk;
+        if (pb) pb[k] = __float2bfloat16_rn(pk);
+    }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ x, long long count, bf16* __restrict__ y)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x)
+        y[k] = __float2bfloat16_rn(x[k]);
+}
+
+int grid_of(long long count)
+{
+    long long b = (count + 255) / 256;
+    return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+}
+
+int status(cudaError_t e) { return e == cudaSuccess ? TPF_OK : TPF_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int tpfnet_conv3x3(const void* x, int N, int H, int W, int Cin, const void* wt, const float* bias, int Cout, int relu,
+                   void* y, void* stream)
+{
+    if (!x || !wt || !y || N < 1 || H < 1 || W < 1 || Cin % kKC || Cout % 32) return TPF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int wblocks = (W + kBM - 1) / kBM;
+    if (Cout % 64 == 0) {
+        dim3 grd(wblocks * N * H, Cout / 64);
+        k_conv3x3<64><<<grd, 128, 0, s>>>((const bf16*)x, N, H, W, Cin, (const bf16*)wt, bias, Cout, relu, (bf16*)y);
+    } else {
+        dim3 grd(wblocks * N * H, Cout / 32);
+        k_conv3x3<32><<<grd, 128, 0, s>>>((const bf16*)x, N, H, W, Cin, (const bf16*)wt, bias, Cout, relu, (bf16*)y);
+    }
+    return status(cudaGetLastError());
+}
+
+int tpfnet_conv3x3_dgrad(const void* dz, int N, int H, int W, int Cout, const void* wt, int Cin, void* wflip, void* dx,
+                         void* stream)
+{
+    if (!dz || !wt || !wflip || !dx || Cin % 32 || Cout % kKC) return TPF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_flip_weights<<<grid_of(9LL * Cin * Cout), 256, 0, s>>>((const bf16*)wt, Cin, Cout, (bf16*)wflip);
+    int rc = status(cudaGetLastError());
+    if (rc) return rc;
+    return tpfnet_conv3x3(dz, N, H, W, Cout, wflip, nullptr, Cin, 0, dx, stream);
+}
+
+int tpfnet_conv3x3_wgrad(const void* x, const void* dz, int N, int H, int W, int Cin, int Cout, float* dw, float* db,
+                         void* stream)
+{
+    if (!x || !dz || !dw || Cin % kWN || Cout % 32) return TPF_ERR_INVALID_ARG;
+    const int WM = Cout % 64 == 0 ? 64 : 32;
+    const long long P = (long long)N * H * W;
+    // split the pixels so that the grid fills the GPU a few times over
+    const long long ctas_per_split = 9LL * (Cin / kWN) * (Cout / WM);
+    long long splits = (152LL * 8 + ctas_per_split - 1) / ctas_per_split;
+    const long long maxsplits = (P + kWK - 1) / kWK;
+    if (splits > maxsplits) splits = maxsplits;
+    if (splits < 1) splits = 1;
+    long long per = (P + splits - 1) / splits;
+    per = (per + kWK - 1) / kWK * kWK;
+    splits = (P + per - 1) / per;
+    dim3 grd(Cin / kWN, Cout / WM, 9 * (int)splits);
+    if (WM == 64)
+        k_conv3x3_wgrad<64><<<grd, 128, 0, (cudaStream_t)stream>>>((const bf16*)x, (const bf16*)dz, N, H, W, Cin, Cout,
+                                                                   (int)per, dw, db);
+    else
+        k_conv3x3_wgrad<32><<<grd, 128, 0, (cudaStream_t)stream>>>((const bf16*)x, (const bf16*)dz, N, H, W, Cin, Cout,
+                                                                   (int)per, dw, db);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_relu_mask(void* d, const void* y, long long count, void* stream)
+{
+    k_relu_mask<<<grid_of(count), 256, 0, (cudaStream_t)stream>>>((bf16*)d, (const bf16*)y, count);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_pool(const void* x, int N, int H, int W, int C, void* y, void* stream)
+{
+    if (H % 2 || W % 2) return TPF_ERR_INVALID_ARG;
+    k_pool<<<grid_of((long long)N * H * W * C / 4), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, N, H, W, C, (bf16*)y);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_pool_back(const void* dy, int N, int H, int W, int C, void* dx, int accumulate, void* stream)
+{
+    k_pool_back<<<grid_of((long long)N * H * W * C), 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, N, H, W, C, (bf16*)dx,
+                                                                                    accumulate);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_up_into(const void* x, int N, int H, int W, int C, void* y, int Ctot, int cofs, void* stream)
+{
+    k_up_into<<<grid_of((long long)N * H * W * C), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, N, H, W, C, (bf16*)y,
+                                                                                  Ctot, cofs);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_up_back(const void* dy, int N, int H, int W, int Ctot, int cofs, int C, void* dx, void* stream)
+{
+    k_up_back<<<grid_of((long long)N * H * W * C / 4), 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, N, H, W, Ctot, cofs,
+                                                                                       C, (bf16*)dx);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_channels(const void* src, int Sc, int sofs, long long pixels, int C, void* dst, int Dc, int dofs,
+                    int accumulate, void* stream)
+{
+    k_channels<<<grid_of(pixels * C), 256, 0, (cudaStream_t)stream>>>((const bf16*)src, Sc, sofs, pixels, C, (bf16*)dst, Dc,
+                                                                     dofs, accumulate);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_head(const void* x, long long pixels, int C, const float* Wt, const float* b, int Cout, float* out,
+                void* stream)
+{
+    k_head<<<grid_of(pixels * Cout), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, pixels, C, Wt, b, Cout, out);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_head_back(const void* x, const float* dout, long long pixels, int C, const float* Wt, int Cout, void* dx,
+                     float* dW, float* db, void* stream)
+{
+    const int smem = (C * Cout + Cout) * (int)sizeof(float);
+    if (smem > 48 * 1024) return TPF_ERR_INVALID_ARG;
+    k_head_back<<<grid_of(pixels) < 304 ? grid_of(pixels) : 304, 256, smem, (cudaStream_t)stream>>>(
+        (const bf16*)x, dout, pixels, C, Wt, Cout, (bf16*)dx, dW, db);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_mse(const float* pred, const float* target, const float* wch, long long count, int C, float* grad,
+               double* loss, void* stream)
+{
+    k_mse<<<grid_of(count) < 1024 ? grid_of(count) : 1024, 256, 0, (cudaStream_t)stream>>>(pred, target, wch, count, C, grad,
+                                                                                          loss);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_adam(float* p, const float* g, float* m, float* v, long long count, float lr, float b1, float b2, float eps,
+                int step, void* pb, void* stream)
+{
+    const float c1 = 1.f / (1.f - powf(b1, (float)step)), c2 = 1.f / (1.f - powf(b2, (float)step));
+    k_adam<<<grid_of(count), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, count, lr, b1, b2, eps, c1, c2, (bf16*)pb);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_to_bf16(const float* x, long long count, void* y, void* stream)
+{
+    k_to_bf16<<<grid_of(count), 256, 0, (cudaStream_t)stream>>>(x, count, (bf16*)y);
+    return status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and
-exports every entry point include/tpflbm.h declares (no compute calls)."""
+exports every entry point that include/tpflbm.h and include/tpfnet.h declare, each
+with a binding signature (no compute calls)."""
 import ctypes as C
 import os
 import re
@@ -9,21 +10,31 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "tpflbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tpflbm_[a-z_0-9]+)\s*\(", src)))
+HEADERS = ("tpflbm.h", "tpfnet.h")
+
+
+def _declared(header=None):
+    out = set()
+    for h in ([header] if header else HEADERS):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        out |= set(re.findall(r"\b((?:tpflbm|tpfnet)_[a-z_0-9]+)\s*\(", src))
+    return sorted(out)
 
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for n in ("tpflbm_create", "tpflbm_init", "tpflbm_step", "tpflbm_get_fields", "tpflbm_destroy"):
+    for n in ("tpflbm_create", "tpflbm_init", "tpflbm_step", "tpflbm_get_fields", "tpflbm_destroy",
+              "tpflbm_batch_step", "tpfnet_conv3x3", "tpfnet_conv3x3_wgrad", "tpfnet_adam"):
         assert n in names
 
 
 def test_library_exports_every_declared_symbol():
     from paper_2306_11320_gb300.build import build_library
-    from paper_2306_11320_gb300.tpflbm import SIGNATURES
+    from paper_2306_11320_gb300.tpflbm import SIGNATURES as S1
+    from paper_2306_11320_gb300.unet import SIGNATURES as S2
+
+    SIGNATURES = dict(S1, **S2)
 
     path = build_library()
     try:

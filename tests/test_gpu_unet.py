@@ -1,0 +1,259 @@
+"""The warm-start U-Net's kernels through the C-ABI (needs a GB300), against the FP64
+numpy reference: each layer kernel on bf16-representable inputs, then the whole
+network's loss and every parameter gradient, then a short training run.
+
+Tolerances follow from the arithmetic: operands are bf16 values that both sides see
+exactly, the GPU accumulates in float32 and rounds each activation it stores to bf16
+(relative half-ulp 2^-9), so one layer differs from FP64 by at most about 2^-8 of its
+output; through the 15 layers of the network these roundings add up to about 1% of
+the output and a few % of the deepest gradients."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import unet_ref as U
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _lib():
+    from paper_2306_11320_gb300.unet import net_library
+
+    return net_library()
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _bf(a):
+    """bf16 CUDA tensor of a float array, and the same values as float64 numpy."""
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).cuda()
+    return t, t.float().cpu().numpy().astype(np.float64)
+
+
+def _np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _w_ref(wt):
+    """[9][Cout][Cin] -> W[dh][dw][ci][co]."""
+    nine, co, ci = wt.shape
+    return wt.reshape(3, 3, co, ci).transpose(0, 1, 3, 2)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _close_bf16(got, ref, relu=False):
+    """Element-wise: bf16 output rounding (2^-8 relative) plus float32 accumulation."""
+    tol = 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), (int(bad.sum()), float(np.abs(got - ref).max()))
+
+
+@pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 6, 80, 64, 96), (1, 4, 64, 32, 128), (1, 3, 8, 96, 64)])
+@pytest.mark.parametrize("relu", [0, 1])
+def test_conv3x3_forward(N, H, W, Cin, Cout, relu):
+    rng = np.random.default_rng(N * 100 + W + relu)
+    lib, s = _lib(), torch.cuda.current_stream().cuda_stream
+    x, xr = _bf(rng.standard_normal((N, H, W, Cin)))
+    wt, wr = _bf(rng.standard_normal((9, Cout, Cin)) / np.sqrt(9 * Cin))
+    b = torch.from_numpy(rng.standard_normal(Cout).astype(np.float32)).cuda()
+    y = torch.empty((N, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    assert lib.tpfnet_conv3x3(_p(x), N, H, W, Cin, _p(wt), _p(b), Cout, relu, _p(y), C.c_void_p(s)) == 0
+    torch.cuda.synchronize()
+    ref = U.conv3x3(xr, _w_ref(wr), b.cpu().numpy().astype(np.float64))
+    if relu:
+        ref = np.maximum(ref, 0)
+    _close_bf16(_np(y), ref)
+
+
+@pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 6, 80, 64, 96), (1, 5, 16, 32, 64)])
+def test_conv3x3_data_and_weight_gradients(N, H, W, Cin, Cout):
+    rng = np.random.default_rng(7 + W)
+    lib, s = _lib(), C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    x, xr = _bf(rng.standard_normal((N, H, W, Cin)))
+    dz, dzr = _bf(rng.standard_normal((N, H, W, Cout)))
+    wt, wr = _bf(rng.standard_normal((9, Cout, Cin)) / np.sqrt(9 * Cin))
+    dx = torch.empty((N, H, W, Cin), dtype=torch.bfloat16, device="cuda")
+    wflip = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+    assert lib.tpfnet_conv3x3_dgrad(_p(dz), N, H, W, Cout, _p(wt), Cin, _p(wflip), _p(dx), s) == 0
+    # weight gradients are ADDED: start from a known value
+    dw0 = rng.standard_normal((9, Cout, Cin)).astype(np.float32)
+    db0 = rng.standard_normal(Cout).astype(np.float32)
+    dw = torch.from_numpy(dw0).cuda()
+    db = torch.from_numpy(db0).cuda()
+    assert lib.tpfnet_conv3x3_wgrad(_p(x), _p(dz), N, H, W, Cin, Cout, _p(dw), _p(db), s) == 0
+    torch.cuda.synchronize()
+    dxr, dWr, dbr = U.conv3x3_backward(xr, _w_ref(wr), dzr)
+    _close_bf16(_np(dx), dxr)
+    # float32 sums over N H W pixels in any order
+    gw = dw.cpu().numpy().astype(np.float64) - dw0
+    ref_w = dWr.transpose(0, 1, 3, 2).reshape(9, Cout, Cin)
+    scale = np.sqrt(N * H * W)
+    assert np.abs(gw - ref_w).max() <= 1e-5 * scale * (1 + np.abs(dw0).max())
+    gb = db.cpu().numpy().astype(np.float64) - db0
+    assert np.abs(gb - dbr).max() <= 1e-5 * scale * (1 + np.abs(db0).max())
+
+
+def test_pool_up_channels_and_adjoints():
+    rng = np.random.default_rng(11)
+    lib, s = _lib(), C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    N, H, W, Cc = 2, 8, 12, 32
+    x, xr = _bf(rng.standard_normal((N, H, W, Cc)))
+    y = torch.empty((N, H // 2, W // 2, Cc), dtype=torch.bfloat16, device="cuda")
+    assert lib.tpfnet_pool(_p(x), N, H, W, Cc, _p(y), s) == 0
+    # the 4-term float32 sum of bf16 values is exact: one rounding to bf16, as in FP64
+    ref = torch.from_numpy(U.pool(xr)).to(torch.bfloat16).double().numpy()
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(y), ref)
+    # pool_back, accumulating onto x
+    dy, dyr = _bf(rng.standard_normal((N, H // 2, W // 2, Cc)))
+    acc = x.clone()
+    assert lib.tpfnet_pool_back(_p(dy), N, H, W, Cc, _p(acc), 1, s) == 0
+    ref = torch.from_numpy(xr + U.pool_backward(dyr)).to(torch.bfloat16).double().numpy()
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(acc), ref)
+    # up into channels [16, 48) of a 64-channel tensor, and its adjoint
+    cat = torch.zeros((N, H, W, 64), dtype=torch.bfloat16, device="cuda")
+    assert lib.tpfnet_up_into(_p(dy), N, H, W, Cc, _p(cat), 64, 16, s) == 0
+    torch.cuda.synchronize()
+    c = _np(cat)
+    assert np.array_equal(c[..., 16:48], U.up(dyr)) and not c[..., :16].any() and not c[..., 48:].any()
+    back = torch.empty((N, H // 2, W // 2, Cc), dtype=torch.bfloat16, device="cuda")
+    g, gr = _bf(rng.standard_normal((N, H, W, 64)))
+    assert lib.tpfnet_up_back(_p(g), N, H, W, 64, 16, Cc, _p(back), s) == 0
+    ref = torch.from_numpy(U.up_backward(gr[..., 16:48])).to(torch.bfloat16).double().numpy()
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(back), ref)
+    # channel copy and accumulate
+    dst = torch.zeros((N, H, W, 96), dtype=torch.bfloat16, device="cuda")
+    assert lib.tpfnet_channels(_p(g), 64, 32, N * H * W, 32, _p(dst), 96, 64, 0, s) == 0
+    assert lib.tpfnet_channels(_p(g), 64, 32, N * H * W, 32, _p(dst), 96, 64, 1, s) == 0
+    torch.cuda.synchronize()
+    d = _np(dst)
+    assert np.array_equal(d[..., 64:], 2 * gr[..., 32:64]) and not d[..., :64].any()
+
+
+def test_head_mse_and_adam():
+    rng = np.random.default_rng(5)
+    lib, s = _lib(), C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    P_, Cc, Co = 1000, 32, 4
+    x, xr = _bf(rng.standard_normal((P_, Cc)))
+    Wt = rng.standard_normal((Cc, Co)).astype(np.float32)
+    b = rng.standard_normal(Co).astype(np.float32)
+    Wd, bd = torch.from_numpy(Wt).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty((P_, Co), dtype=torch.float32, device="cuda")
+    assert lib.tpfnet_head(_p(x), P_, Cc, _p(Wd), _p(bd), Co, _p(out), s) == 0
+    ref = xr @ Wt.astype(np.float64) + b
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+    # MSE and its gradient
+    tgt = torch.from_numpy(rng.standard_normal((P_, Co)).astype(np.float32)).cuda()
+    wch = torch.tensor([1.0, 0.5, 2.0, 1.0], device="cuda")
+    grad = torch.empty_like(out)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert lib.tpfnet_mse(_p(out), _p(tgt), _p(wch), P_ * Co, Co, _p(grad), _p(loss), s) == 0
+    torch.cuda.synchronize()
+    o64, t64, w64 = out.cpu().numpy().astype(np.float64), tgt.cpu().numpy().astype(np.float64), wch.cpu().numpy()
+    ref_loss = np.mean((o64 - t64) ** 2 * w64)
+    assert abs(loss.item() - ref_loss) <= 1e-6 * ref_loss
+    ref_grad = 2 * (o64 - t64) * w64 / o64.size
+    assert np.abs(grad.cpu().numpy() - ref_grad).max() <= 1e-6 * np.abs(ref_grad).max()
+    # head backward: dx overwritten, dW and db added
+    dx = torch.empty((P_, Cc), dtype=torch.bfloat16, device="cuda")
+    dW = torch.ones((Cc, Co), dtype=torch.float32, device="cuda")
+    db = torch.ones(Co, dtype=torch.float32, device="cuda")
+    assert lib.tpfnet_head_back(_p(x), _p(grad), P_, Cc, _p(Wd), Co, _p(dx), _p(dW), _p(db), s) == 0
+    torch.cuda.synchronize()
+    g64 = grad.cpu().numpy().astype(np.float64)
+    _close_bf16(_np(dx), g64 @ Wt.T.astype(np.float64))
+    rW = xr.T @ g64
+    assert np.abs(dW.cpu().numpy() - 1 - rW).max() <= 1e-5 * np.abs(rW).max() + 1e-7
+    assert np.abs(db.cpu().numpy() - 1 - g64.sum(0)).max() <= 1e-5 * np.abs(g64).sum(0).max() + 1e-7
+    # two Adam steps against the textbook update
+    n = 1000
+    p0 = rng.standard_normal(n).astype(np.float32)
+    gs = [rng.standard_normal(n).astype(np.float32) for _ in range(2)]
+    p, m, v = torch.from_numpy(p0.copy()).cuda(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    pb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    pr, mr, vr = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step, gk in enumerate(gs, start=1):
+        gd = torch.from_numpy(gk).cuda()
+        assert lib.tpfnet_adam(_p(p), _p(gd), _p(m), _p(v), n, 1e-2, 0.9, 0.999, 1e-8, step, _p(pb), s) == 0
+        mr = 0.9 * mr + 0.1 * gk
+        vr = 0.999 * vr + 0.001 * gk.astype(np.float64) ** 2
+        pr = pr - 1e-2 * (mr / (1 - 0.9 ** step)) / (np.sqrt(vr / (1 - 0.999 ** step)) + 1e-8)
+    torch.cuda.synchronize()
+    assert np.abs(p.cpu().numpy() - pr).max() <= 1e-5
+    assert torch.equal(pb, p.to(torch.bfloat16))
+
+
+CH = (32, 64, 64, 64)
+
+
+def _small_net(seed=0):
+    """A small network, its parameters rounded to what the GPU stores (3x3 weights in
+    bf16, the rest float32), shared by both sides."""
+    from paper_2306_11320_gb300.unet import UNet
+
+    cin, cout = 3, 4
+    params = U.init_params(cin, cout, CH, seed=seed)
+    for k in params:
+        dt = torch.bfloat16 if (k.endswith(".W") and not k.startswith("head")) else torch.float32
+        params[k] = torch.from_numpy(params[k]).to(dt).double().numpy()
+    net = UNet(cin, cout, CH, seed=seed)
+    net.set_reference_params(params)
+    return net, params
+
+
+def _batch(rng, N=2, H=16, W=64, cin=3):
+    x = np.zeros((N, H, W, 32))
+    x[..., :cin] = rng.standard_normal((N, H, W, cin))
+    xt, xr = _bf(x)
+    return xt, xr[..., :cin]
+
+
+def test_network_loss_and_gradients_match_reference():
+    rng = np.random.default_rng(21)
+    net, params = _small_net()
+    xt, xr = _batch(rng)
+    tgt = rng.standard_normal((2, 16, 64, 4))
+    wch = np.array([1.0, 1.0, 0.5, 2.0])
+    net.zero_grad()
+    out = net.forward(xt)
+    loss = net.mse(out, torch.from_numpy(tgt.astype(np.float32)).cuda(),
+                   torch.from_numpy(wch.astype(np.float32)).cuda())
+    net.backward(net.D["out"])
+    torch.cuda.synchronize()
+    ref_out = U.forward(params, xr)
+    ref_loss, ref_g = U.loss_and_grads(params, xr, tgt.astype(np.float32).astype(np.float64), wch)
+    assert rel_l2(out.cpu().numpy().astype(np.float64), ref_out) <= 2e-2
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss
+    g = net.reference_grads()
+    errs = {k: rel_l2(g[k], ref_g[k]) for k in ref_g}
+    print("gradient rel-L2:", {k: "%.1e" % e for k, e in errs.items()})
+    # gradients pass through up to 30 bf16 roundings (activations forward, gradients
+    # backward): measured 4e-4 at the head growing to 5.5e-2 at the deepest encoder
+    # layer; a wiring mistake (a swapped skip, a missing term) gives O(1) errors
+    for k, e in errs.items():
+        assert e <= 0.1, (k, e)
+
+
+def test_training_reduces_loss():
+    """Adam on a fixed batch with a smooth target the network can represent."""
+    rng = np.random.default_rng(3)
+    net, _ = _small_net(seed=1)
+    xt, xr = _batch(rng)
+    k = np.ones(5) / 5
+    tgt = np.stack([np.apply_along_axis(lambda r: np.convolve(r, k, mode="same"), 2, xr[..., c % 3])
+                    for c in range(4)], axis=-1)
+    tt = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    losses = [net.train_step(xt, tt, lr=2e-3) for _ in range(60)]
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.3 * losses[0], losses[::10]
