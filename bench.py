@@ -34,8 +34,8 @@ NX, NY = 2048, 512
 WORKLOAD = "bubbles_2048x512"
 # algorithmic bytes per lattice update: every population read once and written once
 # (27 x 2 x element size) plus the previous (phi u) read and written (2 x 2 x 4 B);
-# FP16 storage adds the float32 references phi, T of each node (read and written)
-ALG_BYTES = {"fp32": 27 * 2 * 4 + 16, "fp16": 27 * 2 * 2 + 16 + 16}
+# FP16 storage adds the float32 references phi, T, p of each node (read and written)
+ALG_BYTES = {"fp32": 27 * 2 * 4 + 16, "fp16": 27 * 2 * 2 + 16 + 24}
 CPU_SAMPLE_SECONDS = 15.0
 
 
@@ -266,6 +266,73 @@ def bench_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def bench_ensemble(args, rank, world, local_rank):
+    """256 independent lattices of 64x64 to 512x256 nodes (microchannel and drop,
+    Ma 0.01-50, viscosity and conductivity ratios 0.1-10), one batched launch per
+    step replayed from CUDA graphs, tile shape chosen by the autotuner.  Each rank
+    runs its own copy of the ensemble."""
+    import numpy as np
+    import torch
+
+    from paper_2306_11320_gb300 import workloads as WL
+    from paper_2306_11320_gb300.tpflbm import STORAGE_FP16, STORAGE_FP32, Batch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    storage = STORAGE_FP16 if args.storage == "fp16" else STORAGE_FP32
+    members = WL.ensemble(n=256, seed=0)
+    lats = []
+    for p, f, m in members:
+        if storage == STORAGE_FP16:
+            p = dict(p, **WL.fp16_scales(p))
+        lats.append((m["nx"], m["ny"], p))
+    stream = torch.cuda.Stream(device=dev)
+    b = Batch(lats, storage=storage, stream=stream)
+    for k, (p, f, m) in enumerate(members):
+        b.init(k, **{n: v.astype(np.float32) for n, v in f.items()})
+    best, ms = b.tune(steps=10)
+    nodes = sum(nx * ny for nx, ny, _ in lats)
+    steps = max(2, args.steps - args.steps % 2)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        b.step(2 * max(2, args.warmup))
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            e0.record(stream)
+            b.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    d, rc = b.diagnostics()
+    if rank != 0:
+        return
+    shapes = Batch.variants(b.lib)
+    alg = ALG_BYTES[args.storage] * nodes
+    peak, peak_kind = _peaks()
+    achieved = alg / (total_ms * 1e-3 / steps) / 1e9
+    line = {
+        "metric": "coupled-LBM MLUPS", "value": nodes * steps * world / (total_ms * 1e-3) / 1e6, "unit": "MLUPS",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ensemble_256", "lattices": len(lats), "nodes": nodes, "storage": args.storage,
+                   "tile": "%dx%d" % shapes[best], "tune_ms_per_step": ms,
+                   "l2": "state %.0f MB > L2 (steps timed back to back)" % (2 * alg / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "alg_bytes_per_launch": alg, "kernel": "k_step_batch"},
+        "gpu_launches": steps,
+        "clocks": clk.summary(),
+        "check": {"nonfinite_lattices": int((d[:, 7] > 0).sum()), "rc": rc},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,6 +341,9 @@ def main():
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--workload", choices=("bubbles", "ensemble"), default="bubbles",
+                    help="bubbles: the 2048x512 channel (the headline line); ensemble: the "
+                         "256-lattice parameter sweep through the batched launch")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -288,7 +358,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        bench_ours(args, rank, world, local_rank)
+        if args.workload == "ensemble":
+            bench_ensemble(args, rank, world, local_rank)
+        else:
+            bench_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

@@ -63,9 +63,15 @@ typedef struct tpflbm *tpflbm_t;
  *       T_bottom(x) = T_bot + T_bot_amp cos(2 pi T_bot_k x / nx) + T_bot_slope x,
  *       T_top(x) = T_top + T_top_slope x (Sec. 4.1-4.3); 1: periodic in y.
  *   storage: TPF_STORAGE_FP32 or TPF_STORAGE_FP16.  With FP16 a population q_i of
- *       LBE k is stored in float16 as s_k (q_i - r_i), its deviation from the rest
- *       equilibrium of its node at the previous time level: r_i = w_i phi for f,
- *       w_i T for h, 0 for g (phi and T of every node are kept in float32 for this).
+ *       LBE k is stored in float16 as s_k (q_i - r_i), its deviation from a
+ *       reference that the node it streamed from leaves for it: the rest
+ *       equilibrium plus the first-order term of what that node emitted,
+ *       r_i = w_i (phi + c_i . J_f / cs2) for f, w_i (T + c_i . J_h / cs2) for h
+ *       (J the first moment of the post-collision populations; the J term is
+ *       dropped for populations reflected at a boundary), w_i p / cs2 (i != 0) and
+ *       (w_0 - 1) p / cs2 (i = 0) for g.  Each node keeps two records of four
+ *       halves for this: (phi, J_fx/cs2, J_fy/cs2, p/cs2) and (T, J_hx/cs2,
+ *       J_hy/cs2, 0).
  *       s_k are powers of two, fp16_scale_f/g/h (0 selects the defaults 1024, 1024,
  *       64).  All arithmetic stays float32.
  */
@@ -142,8 +148,9 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8]);
  *         elements each, [ny][nx] inside a plane; float32, or float16 encoded as in
  *         tpflbm_params.storage when p->storage is TPF_STORAGE_FP16.
  *   plane elements per plane, >= nx * ny.
- *   ref   FP16 storage only: 2 float planes (phi, then T, of every node at the
- *         previous time level) of `plane` elements; NULL for FP32.
+ *   ref   FP16 storage only: the reference records of the previous step, two
+ *         planes of `plane` 8-byte records (four halves each, see
+ *         tpflbm_params.storage); NULL for FP32.
  *   phiu  device pointer, 2 float planes of `plane` elements ((phi u) of the
  *         previous step).
  *   out   8 doubles, host or device memory; same meaning as tpflbm_diagnostics.
@@ -159,7 +166,18 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8]);
  * reads, so nothing needs clearing; calls whose work overlaps on the GPU (for
  * example on two streams) race on it and must be serialised by the caller. */
 int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params *p, const void *pop, long long plane,
-                              const float *ref, const float *phiu, double out[8], void *stream);
+                              const void *ref, const float *phiu, double out[8], void *stream);
+
+/* Steady-state residual (the paper states no convergence criterion; this is the one
+ * the warm-start comparison uses).  With u, T the current fields and u', T' those of
+ * the previous call, K steps earlier, and N = nx * ny:
+ *   out[0] = ||u - u'||_2 / (K ||u||_2),  out[1] = ||T - T'||_2 / (K dT sqrt(N)),
+ *   out[2] = K,
+ * sums accumulated in FP64 on the device.  The call then keeps the current fields for
+ * the next call.  After tpflbm_init the first call has nothing to compare with and
+ * returns out[0] = out[1] = +inf, out[2] = 0.  dT > 0 is the temperature scale (e.g.
+ * the wall temperature difference).  Synchronises the stream. */
+int tpflbm_residual(tpflbm_t h, double dT, double out[3]);
 
 /* Number of time steps taken since tpflbm_init. */
 long long tpflbm_time(tpflbm_t h);

@@ -22,7 +22,7 @@ namespace {
 struct InstDesc {
     DevParams P;
     void* pop[2];
-    float* ref[2];
+    RefT* ref[2];
     float* phiu;
 };
 
@@ -54,7 +54,7 @@ k_step_batch(const InstDesc* __restrict__ inst, const int2* __restrict__ work, i
         __syncthreads();
         const typename S::elem* A = (const typename S::elem*)bufs[0];
         typename S::elem* B = (typename S::elem*)bufs[1];
-        step_tile_general<BX, BY, S>(P, A, B, (float*)bufs[4], (const float*)bufs[2], (float*)bufs[3], sm,
+        step_tile_general<BX, BY, S>(P, A, B, (float*)bufs[4], (const RefT*)bufs[2], (RefT*)bufs[3], sm,
                                      item.y & 0xffff, item.y >> 16);
         // step_tile_general ends with a barrier: P and bufs are free again
     }

@@ -20,12 +20,14 @@ struct tpflbm {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     void* pop[2] = {nullptr, nullptr};  // population buffers; pop[cur] holds time t
-    float* ref[2] = {nullptr, nullptr}; // FP16 references, paired with pop
+    tpf::RefT* ref[2] = {nullptr, nullptr}; // FP16 reference records, paired with pop
     int cur = 0;
     float* phiu = nullptr;
     float* stage = nullptr;             // 9 float planes: fields and state I/O
     double* red = nullptr;              // per-block partials and results of the reductions
     int* err = nullptr;                 // device error flag of the step kernels
+    float* snap = nullptr;              // u_x, u_y, T at the last residual call
+    long long snap_t = -1;              // its time step (-1: none)
     // TMA step kernel
     bool tma = false;
     tpf::TmaMaps maps[2]{};             // maps[c]: reading pop[c]

@@ -14,6 +14,8 @@ __host__ __device__ constexpr int cx(int i) { return (i == 1 || i == 5 || i == 8
 __host__ __device__ constexpr int cy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
 __host__ __device__ constexpr float wq(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+// pressure weight of the NS equilibrium at rest: g_i^eq(u = 0) = wg(i) p / cs2
+__host__ __device__ constexpr float wg(int i) { return i == 0 ? 4.f / 9.f - 1.f : wq(i); }
 constexpr float kCs2 = 1.f / 3.f;
 constexpr float kInvCs2 = 3.f;
 

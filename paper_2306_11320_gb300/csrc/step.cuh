@@ -13,23 +13,61 @@
 
 namespace tpf {
 
-// FP16 storage keeps the scaled deviation s_k (q_i - r_i) of each population from
-// the rest equilibrium of the node it streamed from: r_i = w_i phi(src) for f,
-// w_i T(src) for h, 0 for g, with src = y - c_i (wrapped when periodic) and src = y
-// itself when y - c_i lies outside the fluid (a population reflected at a wall, the
-// inlet or the outflow plane).  phi and T of every node at the previous time level
-// are kept in two float planes ("ref").  The writer of a population is its source
-// node, so it encodes with its own phi and T.
+// FP16 storage keeps the scaled deviation s_k (q_i - r_i) of each population from a
+// reference r_i built from a record that the population's writer (its source node
+// y - c_i, wrapped when periodic) leaves for the next step:
+//   f: r_i = w_i (phi + c_i . J_f / cs2)      h: r_i = w_i (T + c_i . J_h / cs2)
+//   g: r_i = w_i p / cs2 (i != 0), (w_0 - 1) p / cs2 (i = 0)
+// with phi, T, p the writer's moments and J_f, J_h the first moments of its
+// post-collision f and h, i.e. the rest equilibrium plus the first-order Hermite term
+// of what it emitted, so that only the higher-order non-equilibrium part is
+// quantised.  A population whose source lies outside the fluid (reflected at a wall,
+// the inlet or the outflow plane) was written by the node that holds it, and its
+// reference drops the first-moment term.  Each record is four halves (phi, J_fx/cs2,
+// J_fy/cs2, p/cs2) and (T, J_hx/cs2, J_hy/cs2, 0); the writer encodes against the
+// rounded record, so encoder and decoder see the same reference bit for bit.
 template <class S>
 constexpr bool kRef = std::is_same<S, StoreF16>::value;
 
-// node whose rest equilibrium is the FP16 reference of population i at (x, y)
-__device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int i)
+using RefT = uint2;  // one reference record: four halves
+
+struct RefVals {
+    float m0, jx, jy, w;
+};
+__device__ __forceinline__ RefVals ref_unpack(RefT q)
+{
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    return {a.x, a.y, b.x, b.y};
+}
+// rounds (m0, jx, jy, w) to halves; r receives the rounded values
+__device__ __forceinline__ RefT ref_pack(float m0, float jx, float jy, float w, RefVals& r)
+{
+    const __half2 a = __floats2half2_rn(m0, jx), b = __floats2half2_rn(jy, w);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    r = {fa.x, fa.y, fb.x, fb.y};
+    RefT q;
+    q.x = *reinterpret_cast<const uint32_t*>(&a);
+    q.y = *reinterpret_cast<const uint32_t*>(&b);
+    return q;
+}
+__device__ __forceinline__ float half_round(float v) { return __half2float(__float2half_rn(v)); }
+
+// reference of population i of f or h from its writer's record
+__device__ __forceinline__ float ref_pop(int i, const RefVals& r, bool self)
+{
+    return self ? wq(i) * r.m0 : wq(i) * (r.m0 + (float)cx(i) * r.jx + (float)cy(i) * r.jy);
+}
+
+// node whose record is the FP16 reference of population i at (x, y); self is set when
+// y - c_i lies outside the fluid (the node itself wrote the population)
+__device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int i, bool& self)
 {
     int sx = x - cx(i), sy = y - cy(i);
     if (P.bc_x == 0) sx = wrap(sx, P.nx);
     if (P.bc_y == 1) sy = wrap(sy, P.ny);
-    if (sx < 0 || sx >= P.nx || sy < 0 || sy >= P.ny) {
+    self = sx < 0 || sx >= P.nx || sy < 0 || sy >= P.ny;
+    if (self) {
         sx = x;
         sy = y;
     }
@@ -39,22 +77,26 @@ __device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int 
 // Decoded populations of node (x, y) read from global memory (general path).
 template <class S, bool WANT_G = true>
 __device__ __forceinline__ void load_node(const DevParams& P, const typename S::elem* __restrict__ A,
-                                          const float* __restrict__ ref, int x, int y, float* f, float* g,
+                                          const RefT* __restrict__ ref, int x, int y, float* f, float* g,
                                           float* h)
 {
     const long long pl = P.plane;
     const int n = y * P.nx + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        float rp = 0.f, rt = 0.f;
+        float rf = 0.f, rg = 0.f, rh = 0.f;
         if constexpr (kRef<S>) {
-            const int s = ref_source(P, x, y, i);
-            rp = ref[s];
-            rt = ref[pl + s];
+            bool self;
+            const int s = ref_source(P, x, y, i, self);
+            const RefVals a = ref_unpack(ref[s]);
+            const RefVals b = ref_unpack(ref[pl + s]);
+            rf = ref_pop(i, a, self);
+            rg = wg(i) * a.w;
+            rh = ref_pop(i, b, self);
         }
-        f[i] = S::ld(A + i * pl, n, P.is_f, wq(i) * rp);
-        if constexpr (WANT_G) g[i] = S::ld(A + (9 + i) * pl, n, P.is_g, 0.f);
-        h[i] = S::ld(A + (18 + i) * pl, n, P.is_h, wq(i) * rt);
+        f[i] = S::ld(A + i * pl, n, P.is_f, rf);
+        if constexpr (WANT_G) g[i] = S::ld(A + (9 + i) * pl, n, P.is_g, rg);
+        h[i] = S::ld(A + (18 + i) * pl, n, P.is_h, rh);
     }
 }
 
@@ -69,27 +111,46 @@ struct RingSmem {
 };
 
 // Collide the node's populations and push them to their destinations, with every
-// boundary rule.  hold(i, k) and irc(k) give the pre-collision h_i and 1/(rho c_p)
-// of the node in ring slot k; phiR(k), TR(k) its phi and T.
+// boundary rule; for FP16 also leave the node's reference records in refB.
+// hold(i, k) and irc(k) give the pre-collision h_i and 1/(rho c_p) of the node in
+// ring slot k; phiR(k), TR(k) its phi and T.
 template <class S, int SX, class HOLD, class IRC, class PHIR, class TR>
-__device__ __forceinline__ void collide_push(const DevParams& P, typename S::elem* __restrict__ B, int x, int y,
-                                             int kown, bool interior, const Macro& m, float* f, float* g,
-                                             float* h, HOLD hold, IRC irc, PHIR phiR, TR TR_)
+__device__ __forceinline__ void collide_push(const DevParams& P, typename S::elem* __restrict__ B,
+                                             RefT* __restrict__ refB, int x, int y, int kown, bool interior,
+                                             const Macro& m, float* f, float* g, float* h, HOLD hold, IRC irc,
+                                             PHIR phiR, TR TR_)
 {
     const long long pl = P.plane;
     const int n = y * P.nx + x;
     node_collide(P, m, f, g, h);
-    // FP16 references: the writer's own rest equilibrium
-    const float rp = kRef<S> ? m.phi : 0.f, rt = kRef<S> ? m.T : 0.f;
+    // FP16 reference records of what this node emits (rounded values in rf, rh)
+    RefVals rf{0.f, 0.f, 0.f, 0.f}, rh{0.f, 0.f, 0.f, 0.f};
+    if constexpr (kRef<S>) {
+        float jfx = 0.f, jfy = 0.f, jhx = 0.f, jhy = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (cx(i) != 0) {
+                jfx += (float)cx(i) * f[i];
+                jhx += (float)cx(i) * h[i];
+            }
+            if (cy(i) != 0) {
+                jfy += (float)cy(i) * f[i];
+                jhy += (float)cy(i) * h[i];
+            }
+        }
+        refB[n] = ref_pack(m.phi, jfx * kInvCs2, jfy * kInvCs2, m.p * kInvCs2, rf);
+        refB[pl + n] = ref_pack(m.T, jhx * kInvCs2, jhy * kInvCs2, 0.f, rh);
+    }
+    const float rg = rf.w;
     if (interior) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int d = n + cy(i) * P.nx + cx(i);
             const int kd = kown + cy(i) * SX + cx(i);
-            S::st(B + i * pl, d, f[i], P.s_f, wq(i) * rp);
-            S::st(B + (9 + i) * pl, d, g[i], P.s_g, 0.f);
+            S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf, false));
+            S::st(B + (9 + i) * pl, d, g[i], P.s_g, wg(i) * rg);
             const float ho = hold(i, kd);
-            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, wq(i) * rt);
+            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh, false));
         }
         return;
     }
@@ -107,45 +168,47 @@ __device__ __forceinline__ void collide_push(const DevParams& P, typename S::ele
             // temperature at the link's crossing point
             const float xc = (float)x + 0.5f * cx(i);
             const float Tw = (cy(i) < 0) ? T_wall_bottom(P, xc) : T_wall_top(P, xc);
-            S::st(B + o * pl, n, f[i], P.s_f, wq(o) * rp);
-            S::st(B + (9 + o) * pl, n, g[i], P.s_g, 0.f);
+            S::st(B + o * pl, n, f[i], P.s_f, ref_pop(o, rf, true));
+            S::st(B + (9 + o) * pl, n, g[i], P.s_g, wg(o) * rg);
             const float ho = hold(o, kown);
             const float hin = -h[i] + 2.f * wq(o) * Tw;
-            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, wq(o) * rt);
+            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, ref_pop(o, rh, true));
         } else if (out_x && dx < 0) {
             // velocity inlet: bounce-back carrying the inlet momentum and phi_in
             const float ycr = (float)y + 0.5f + 0.5f * cy(i);
             const float cu = cx(o) * u_inlet(P, ycr);
-            S::st(B + o * pl, n, f[i] + 2.f * wq(o) * P.phi_in * cu * kInvCs2, P.s_f, wq(o) * rp);
-            S::st(B + (9 + o) * pl, n, g[i] + 2.f * wq(o) * m.rho * cu * kInvCs2, P.s_g, 0.f);
+            S::st(B + o * pl, n, f[i] + 2.f * wq(o) * P.phi_in * cu * kInvCs2, P.s_f, ref_pop(o, rf, true));
+            S::st(B + (9 + o) * pl, n, g[i] + 2.f * wq(o) * m.rho * cu * kInvCs2, P.s_g, wg(o) * rg);
             const float ho = hold(o, kown);
             const float hin = -h[i] + 2.f * wq(o) * P.T_in;
-            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, wq(o) * rt);
+            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, ref_pop(o, rh, true));
         } else if (out_x) {
             // outflow: pressure anti-bounce-back of g (f and h arrive by the copy below)
             const float cu = cx(o) * m.ux + cy(o) * m.uy;
             const float sym = P.p_out * kInvCs2 +
                               m.rho * (0.5f * cu * cu * kInvCs2 * kInvCs2 - 0.5f * (m.ux * m.ux + m.uy * m.uy) * kInvCs2);
-            S::st(B + (9 + o) * pl, n, -g[i] + 2.f * wq(o) * sym, P.s_g, 0.f);
+            S::st(B + (9 + o) * pl, n, -g[i] + 2.f * wq(o) * sym, P.s_g, wg(o) * rg);
         } else {
             const int d = dy * P.nx + dx;
             const int kd = kown + cy(i) * SX + cx(i);
-            S::st(B + i * pl, d, f[i], P.s_f, wq(i) * rp);
-            S::st(B + (9 + i) * pl, d, g[i], P.s_g, 0.f);
+            S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf, false));
+            S::st(B + (9 + i) * pl, d, g[i], P.s_g, wg(i) * rg);
             const float ho = hold(i, kd);
-            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, wq(i) * rt);
+            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh, false));
         }
         // zero-gradient outflow of f and h: the ghost column beyond x = nx-1 carries the
         // post-collision populations of the last column.  The destination decodes them
-        // with its own reference (their source lies outside), so encode with it.
+        // with the zeroth moment of its own record (their source lies outside), so
+        // encode with its rounded phi and T.
         if (P.bc_x == 1 && x == P.nx - 1 && cx(i) < 0) {
             const int ey = y + cy(i);
             if (ey >= 0 && ey < P.ny) {
                 const int d = ey * P.nx + x;
                 const int kd = kown + cy(i) * SX;
-                S::st(B + i * pl, d, f[i], P.s_f, kRef<S> ? wq(i) * phiR(kd) : 0.f);
+                S::st(B + i * pl, d, f[i], P.s_f, kRef<S> ? wq(i) * half_round(phiR(kd)) : 0.f);
                 const float ho = hold(i, kd);
-                S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, kRef<S> ? wq(i) * TR_(kd) : 0.f);
+                S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h,
+                      kRef<S> ? wq(i) * half_round(TR_(kd)) : 0.f);
             }
         }
     }
@@ -157,7 +220,7 @@ __device__ __forceinline__ void collide_push(const DevParams& P, typename S::ele
 template <int BX, int BY, class S>
 __device__ __forceinline__ void step_tile_general(const DevParams& P, const typename S::elem* __restrict__ A,
                                                   typename S::elem* __restrict__ B, float* __restrict__ phiu,
-                                                  const float* __restrict__ refA, float* __restrict__ refB,
+                                                  const RefT* __restrict__ refA, RefT* __restrict__ refB,
                                                   RingSmem<BX, BY>& sm, int bx, int by)
 {
     constexpr int SX = RingSmem<BX, BY>::SX, SN = RingSmem<BX, BY>::SN;
@@ -245,12 +308,8 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
         const Macro m = node_macro(P, f, g, h, phin, Tn, phiu[n], phiu[pl + n]);
         phiu[n] = m.phi * m.ux;
         phiu[pl + n] = m.phi * m.uy;
-        if constexpr (kRef<S>) {
-            refB[n] = m.phi;
-            refB[pl + n] = m.T;
-        }
         collide_push<S, SX>(
-            P, B, x, y, kown, interior, m, f, g, h, [&](int i, int k) { return sm.h[i][k]; },
+            P, B, refB, x, y, kown, interior, m, f, g, h, [&](int i, int k) { return sm.h[i][k]; },
             [&](int k) { return sm.irc[k]; }, [&](int k) { return sm.phi[k]; }, [&](int k) { return sm.T[k]; });
     }
     __syncthreads();  // the caller may reuse sm for the next tile
@@ -259,7 +318,7 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
 template <int BX, int BY, class S>
 __global__ void __launch_bounds__(BX * BY, 3)
 k_step_general(const DevParams P, const typename S::elem* __restrict__ A, typename S::elem* __restrict__ B,
-               float* __restrict__ phiu, const float* __restrict__ refA, float* __restrict__ refB)
+               float* __restrict__ phiu, const RefT* __restrict__ refA, RefT* __restrict__ refB)
 {
     __shared__ RingSmem<BX, BY> sm;
     step_tile_general<BX, BY, S>(P, A, B, phiu, refA, refB, sm, blockIdx.x, blockIdx.y);
@@ -272,8 +331,8 @@ k_step_general(const DevParams P, const typename S::elem* __restrict__ A, typena
 // tiles through the general path.  For a TMA tile one elected thread issues 3D bulk
 // tensor copies (cp.async.bulk.tensor) of the 9 f planes and the 9 h planes over the
 // tile plus a one-node ring (widened to XP columns each side for the 16-byte rule),
-// the 9 g planes and the 2 (phi u) planes over the tile, and for FP16 the 2 reference
-// planes over the tile plus a two-node ring, all completing on one mbarrier.  While a
+// the 9 g planes and the 2 (phi u) planes over the tile, and for FP16 the 2 planes of
+// reference records over the tile plus a two-node ring, all completing on one mbarrier.  While a
 // tile is computed, the next tile's copies are in flight into the other stage.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -326,7 +385,7 @@ struct TmaLayout {
     static constexpr int F_BYTES = 9 * FH * FW * (int)sizeof(E);
     static constexpr int G_BYTES = 9 * BY * BX * (int)sizeof(E);
     static constexpr int U_BYTES = 2 * BY * BX * 4;
-    static constexpr int R_BYTES = kRef<S> ? 2 * RH * RW * 4 : 0;
+    static constexpr int R_BYTES = kRef<S> ? 2 * RH * RW * (int)sizeof(RefT) : 0;
     static constexpr int OFF_F = 0, OFF_H = rnd(F_BYTES), OFF_G = OFF_H + rnd(F_BYTES), OFF_U = OFF_G + rnd(G_BYTES),
                          OFF_R = OFF_U + rnd(U_BYTES), STAGE = OFF_R + rnd(R_BYTES);
     static constexpr uint32_t TX_BYTES = 2 * F_BYTES + G_BYTES + U_BYTES + R_BYTES;
@@ -336,7 +395,7 @@ struct TmaMaps {
     CUtensorMap popF;  // populations, box FW x FH x 9 (used for f at z = 0 and h at z = 18)
     CUtensorMap popG;  // populations, box BX x BY x 9 (g at z = 9)
     CUtensorMap phiu;  // (phi u) planes, box BX x BY x 2
-    CUtensorMap ref;   // FP16 references, box RW x RH x 2
+    CUtensorMap ref;   // FP16 reference records (8-byte elements), box RW x RH x 2
 };
 
 // phi, T and 1/(rho c_p) of a TMA tile and its ring
@@ -355,8 +414,8 @@ constexpr int kTmaMinBlocks = kRef<S> ? 3 : 2;
 template <int BX, int BY, class S>
 __global__ void __launch_bounds__(BX * BY, kTmaMinBlocks<S>)
 k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typename S::elem* __restrict__ A,
-           typename S::elem* __restrict__ B, float* __restrict__ phiu, const float* __restrict__ refA,
-           float* __restrict__ refB, int bx0, int by0, int ntbx, int ntby, int* __restrict__ err)
+           typename S::elem* __restrict__ B, float* __restrict__ phiu, const RefT* __restrict__ refA,
+           RefT* __restrict__ refB, int bx0, int by0, int ntbx, int ntby, int* __restrict__ err)
 {
     using L = TmaLayout<BX, BY, S>;
     using E = typename S::elem;
@@ -416,19 +475,15 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         const E* sH = (const E*)(st + L::OFF_H);
         const E* sG = (const E*)(st + L::OFF_G);
         const float* sU = (const float*)(st + L::OFF_U);
-        const float* sR = (const float*)(st + L::OFF_R);
+        const RefT* sR = (const RefT*)(st + L::OFF_R);
         const int bx = bx0 + t % ntbx, by = by0 + t / ntbx;
         const int x0 = bx * BX, y0 = by * BY;
 
         // decoded population i of ring slot (lx, ly) from the f (or h) box
         auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly) {
-            const float raw = S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, 0.f);
-            if constexpr (kRef<S>) {
-                const float r = sR[(rplane * L::RH + ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i)];
-                return fmaf(wq(i), r, raw);
-            } else {
-                return raw;
-            }
+            float r = 0.f;
+            if constexpr (kRef<S>) r = ref_pop(i, ref_unpack(sR[(rplane * L::RH + ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i)]), false);
+            return S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, r);
         };
 
         // own node: decoded populations, phi, T, 1/(rho c_p)
@@ -441,9 +496,18 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
             float sf = 0.f, sh = 0.f;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = decF(sF, P.is_f, 0, i, lx, ly);
-                h[i] = decF(sH, P.is_h, 1, i, lx, ly);
-                g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, 0.f);
+                float rf = 0.f, rg = 0.f, rh = 0.f;
+                if constexpr (kRef<S>) {
+                    const int k = (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i);
+                    const RefVals a = ref_unpack(sR[k]);
+                    const RefVals b = ref_unpack(sR[L::RH * L::RW + k]);
+                    rf = ref_pop(i, a, false);
+                    rg = wg(i) * a.w;
+                    rh = ref_pop(i, b, false);
+                }
+                f[i] = S::lds(sF, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_f, rf);
+                h[i] = S::lds(sH, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_h, rh);
+                g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, rg);
                 sf += f[i];
                 sh += h[i];
             }
@@ -482,12 +546,8 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
         phiu[n] = m.phi * m.ux;
         phiu[pl + n] = m.phi * m.uy;
-        if constexpr (kRef<S>) {
-            refB[n] = m.phi;
-            refB[pl + n] = m.T;
-        }
         collide_push<S, SX>(
-            P, B, x, y, kown, true, m, f, g, h,
+            P, B, refB, x, y, kown, true, m, f, g, h,
             [&](int i, int kd) { return decF(sH, P.is_h, 1, i, kd % SX, kd / SX); },
             [&](int kd) { return sm.irc[kd]; }, [&](int kd) { return sm.phi[kd]; },
             [&](int kd) { return sm.T[kd]; });

@@ -31,7 +31,7 @@ constexpr int kMaxDevices = 64;
 // Macroscopic state of node (x, y) read straight from global memory.
 template <class S>
 __device__ Macro macro_at(const DevParams& P, const typename S::elem* __restrict__ A,
-                          const float* __restrict__ ref, const float* __restrict__ phiu, int x, int y)
+                          const RefT* __restrict__ ref, const float* __restrict__ phiu, int x, int y)
 {
     const long long pl = P.plane;
     const int n = y * P.nx + x;
@@ -56,7 +56,7 @@ __device__ Macro macro_at(const DevParams& P, const typename S::elem* __restrict
 }
 
 template <class S>
-__global__ void k_fields(const DevParams P, const typename S::elem* __restrict__ A, const float* __restrict__ ref,
+__global__ void k_fields(const DevParams P, const typename S::elem* __restrict__ A, const RefT* __restrict__ ref,
                          const float* __restrict__ phiu, float* __restrict__ out)
 {
     const long long N = (long long)P.nx * P.ny;
@@ -73,11 +73,11 @@ __global__ void k_fields(const DevParams P, const typename S::elem* __restrict__
 }
 
 // Equilibrium populations from the staged fields (planes 0-4: phi, ux, uy, p, T).
-// FP16 references: phi and T of each node (ref planes), each population encoded
-// against its reference node (ref_source).
+// FP16 records: (phi, 0, 0, p / cs2) and (T, 0, 0, 0) of each node, so that every
+// population is encoded against the rest equilibrium of its source (ref_source).
 template <class S>
 __global__ void k_init(const DevParams P, const float* __restrict__ in, typename S::elem* __restrict__ A,
-                       float* __restrict__ ref, float* __restrict__ phiu)
+                       RefT* __restrict__ ref, float* __restrict__ phiu)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
@@ -89,19 +89,22 @@ __global__ void k_init(const DevParams P, const float* __restrict__ in, typename
         node_equilibria(P, phi, ux, uy, p, T, f, g, h);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            float rp = 0.f, rt = 0.f;
+            float rf = 0.f, rg = 0.f, rh = 0.f;
             if constexpr (kRef<S>) {
-                const int s = ref_source(P, x, y, i);
-                rp = in[s];
-                rt = in[4 * pl + s];
+                bool self;
+                const int s = ref_source(P, x, y, i, self);
+                rf = wq(i) * half_round(in[s]);
+                rg = wg(i) * half_round(in[3 * pl + s] * kInvCs2);
+                rh = wq(i) * half_round(in[4 * pl + s]);
             }
-            S::st(A + i * pl, n, f[i], P.s_f, wq(i) * rp);
-            S::st(A + (9 + i) * pl, n, g[i], P.s_g, 0.f);
-            S::st(A + (18 + i) * pl, n, h[i], P.s_h, wq(i) * rt);
+            S::st(A + i * pl, n, f[i], P.s_f, rf);
+            S::st(A + (9 + i) * pl, n, g[i], P.s_g, rg);
+            S::st(A + (18 + i) * pl, n, h[i], P.s_h, rh);
         }
         if constexpr (kRef<S>) {
-            ref[n] = phi;
-            ref[pl + n] = T;
+            RefVals r;
+            ref[n] = ref_pack(phi, 0.f, 0.f, p * kInvCs2, r);
+            ref[pl + n] = ref_pack(T, 0.f, 0.f, 0.f, r);
         }
         phiu[n] = phi * ux;
         phiu[pl + n] = phi * uy;
@@ -109,23 +112,42 @@ __global__ void k_init(const DevParams P, const float* __restrict__ in, typename
 }
 
 // State I/O of one LBE (k = 0 f, 1 g, 2 h) between 9 float32 staging planes and
-// storage.  For FP16, k_lbe_ref first sets each node's reference to the zeroth
-// moment of its staged populations (phi for f, T for h).
-__global__ void k_lbe_ref(const DevParams P, int k, const float* __restrict__ in, float* __restrict__ ref)
+// storage.  For FP16, k_lbe_ref first sets the LBE's part of each node's record from
+// its staged populations: the zeroth moment (phi for f, T for h, first moments 0),
+// and for g the pressure estimate p / cs2 = sum_{i != 0} g_i / (1 - w_0) (Eq. 21
+// without its velocity terms; any value serves as long as encoder and decoder share
+// it).  The other LBEs' parts of the records are left as they are.
+__global__ void k_lbe_ref(const DevParams P, int k, const float* __restrict__ in, RefT* __restrict__ ref)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
+    __half* rh = reinterpret_cast<__half*>(ref);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         float r = 0.f;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) r += in[i * pl + n];
-        ref[(k == 2 ? pl : 0) + n] = r;
+        for (int i = (k == 1 ? 1 : 0); i < 9; ++i) r += in[i * pl + n];
+        if (k == 1) {
+            rh[4 * n + 3] = __float2half_rn(r / (1.f - wq(0)));
+        } else {
+            __half* q = rh + 4 * ((k == 2 ? pl : 0) + n);
+            q[0] = __float2half_rn(r);
+            q[1] = __float2half_rn(0.f);
+            q[2] = __float2half_rn(0.f);
+        }
     }
+}
+// reference of population i of LBE k at (x, y)
+__device__ __forceinline__ float lbe_ref(const DevParams& P, int k, const RefT* __restrict__ ref, int x, int y, int i)
+{
+    bool self;
+    const int s = ref_source(P, x, y, i, self);
+    const RefVals r = ref_unpack(ref[(k == 2 ? P.plane : 0) + s]);
+    return k == 1 ? wg(i) * r.w : ref_pop(i, r, self);
 }
 template <class S>
 __global__ void k_lbe_encode(const DevParams P, int k, const float* __restrict__ in, typename S::elem* __restrict__ A,
-                             const float* __restrict__ ref)
+                             const RefT* __restrict__ ref)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
@@ -135,14 +157,14 @@ __global__ void k_lbe_encode(const DevParams P, int k, const float* __restrict__
         const int x = (int)(n % P.nx), y = (int)(n / P.nx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const float r = (kRef<S> && k != 1) ? ref[(k == 2 ? pl : 0) + ref_source(P, x, y, i)] : 0.f;
-            S::st(A + (9 * k + i) * pl, n, in[i * pl + n], s, wq(i) * r);
+            const float r = kRef<S> ? lbe_ref(P, k, ref, x, y, i) : 0.f;
+            S::st(A + (9 * k + i) * pl, n, in[i * pl + n], s, r);
         }
     }
 }
 template <class S>
 __global__ void k_lbe_decode(const DevParams P, int k, const typename S::elem* __restrict__ A,
-                             const float* __restrict__ ref, float* __restrict__ out)
+                             const RefT* __restrict__ ref, float* __restrict__ out)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
@@ -152,8 +174,8 @@ __global__ void k_lbe_decode(const DevParams P, int k, const typename S::elem* _
         const int x = (int)(n % P.nx), y = (int)(n / P.nx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const float r = (kRef<S> && k != 1) ? ref[(k == 2 ? pl : 0) + ref_source(P, x, y, i)] : 0.f;
-            out[i * pl + n] = S::ld(A + (9 * k + i) * pl, n, is, wq(i) * r);
+            const float r = kRef<S> ? lbe_ref(P, k, ref, x, y, i) : 0.f;
+            out[i * pl + n] = S::ld(A + (9 * k + i) * pl, n, is, r);
         }
     }
 }
@@ -165,7 +187,7 @@ constexpr int kRedMaxBlocks = 1024;
 
 template <class S>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_partial(const DevParams P, const typename S::elem* __restrict__ A, const float* __restrict__ ref,
+k_reduce_partial(const DevParams P, const typename S::elem* __restrict__ A, const RefT* __restrict__ ref,
                  const float* __restrict__ phiu, double* __restrict__ partial)
 {
     const long long N = (long long)P.nx * P.ny;
@@ -210,6 +232,45 @@ __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, 
     }
 }
 
+// Steady-state residual: FP64 sums of |u - u_snap|^2, |u|^2 and (T - T_snap)^2 per
+// block, then the snapshot is overwritten with the current u, T.
+template <class S>
+__global__ void __launch_bounds__(kRedThreads)
+k_residual_partial(const DevParams P, const typename S::elem* __restrict__ A, const RefT* __restrict__ ref,
+                   const float* __restrict__ phiu, float* __restrict__ snap, double* __restrict__ partial)
+{
+    const long long N = (long long)P.nx * P.ny;
+    const long long pl = P.plane;
+    double acc[3] = {0, 0, 0};
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % P.nx), y = (int)(n / P.nx);
+        const Macro m = macro_at<S>(P, A, ref, phiu, x, y);
+        const double dux = (double)m.ux - snap[n], duy = (double)m.uy - snap[pl + n];
+        const double dT = (double)m.T - snap[2 * pl + n];
+        acc[0] += dux * dux + duy * duy;
+        acc[1] += (double)m.ux * m.ux + (double)m.uy * m.uy;
+        acc[2] += dT * dT;
+        snap[n] = m.ux;
+        snap[pl + n] = m.uy;
+        snap[2 * pl + n] = m.T;
+    }
+    __shared__ double red[3][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) v += red[threadIdx.x][w];
+        partial[blockIdx.x * 8 + threadIdx.x] = v;
+    }
+}
+
 }  // namespace
 
 // Scratch of tpflbm_diagnostics_static: the per-block partial sums (kRedMaxBlocks x 8)
@@ -229,7 +290,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 long long plane_of(int nx, int ny) { return (((long long)nx * ny + 63) / 64) * 64; }
 
 struct Layout {
-    size_t pop0, pop1, ref0, ref1, phiu, stage, red, err, total;
+    size_t pop0, pop1, ref0, ref1, phiu, stage, red, err, snap, total;
 };
 
 Layout layout_of(int nx, int ny, int storage)
@@ -241,12 +302,13 @@ Layout layout_of(int nx, int ny, int storage)
     size_t off = 0;
     L.pop0 = off; off = align256(off + 27 * (size_t)pl * e);
     L.pop1 = off; off = align256(off + 27 * (size_t)pl * e);
-    L.ref0 = off; off = align256(off + (f16 ? 2 * (size_t)pl * 4 : 0));
-    L.ref1 = off; off = align256(off + (f16 ? 2 * (size_t)pl * 4 : 0));
+    L.ref0 = off; off = align256(off + (f16 ? 2 * (size_t)pl * sizeof(RefT) : 0));
+    L.ref1 = off; off = align256(off + (f16 ? 2 * (size_t)pl * sizeof(RefT) : 0));
     L.phiu = off; off = align256(off + 2 * (size_t)pl * 4);
     L.stage = off; off = align256(off + kStagePlanes * (size_t)pl * 4);
     L.red = off; off = align256(off + (kRedMaxBlocks * 8 + 8) * sizeof(double));
     L.err = off; off = align256(off + 256);
+    L.snap = off; off = align256(off + 3 * (size_t)pl * 4);
     L.total = off;
     return L;
 }
@@ -395,7 +457,7 @@ void setup_tma(tpflbm_t h)
         bool ok = make_map(&M.popF, dt, e, h->pop[c], nx, ny, 27, pl, L::FW, L::FH, 9) &&
                   make_map(&M.popG, dt, e, h->pop[c], nx, ny, 27, pl, kBX, kBY, 9) &&
                   make_map(&M.phiu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->phiu, nx, ny, 2, pl, kBX, kBY, 2);
-        if (kRef<S>) ok = ok && make_map(&M.ref, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->ref[c], nx, ny, 2, pl, L::RW, L::RH, 2);
+        if (kRef<S>) ok = ok && make_map(&M.ref, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, h->ref[c], nx, ny, 2, pl, L::RW, L::RH, 2);
         else M.ref = M.phiu;
         if (!ok) return;
     }
@@ -426,12 +488,13 @@ int finish_create(tpflbm_t h, int nx, int ny, const tpflbm_params* p, void* ws, 
     char* b = (char*)ws;
     h->pop[0] = b + L.pop0;
     h->pop[1] = b + L.pop1;
-    h->ref[0] = (float*)(b + L.ref0);
-    h->ref[1] = (float*)(b + L.ref1);
+    h->ref[0] = (RefT*)(b + L.ref0);
+    h->ref[1] = (RefT*)(b + L.ref1);
     h->phiu = (float*)(b + L.phiu);
     h->stage = (float*)(b + L.stage);
     h->red = (double*)(b + L.red);
     h->err = (int*)(b + L.err);
+    h->snap = (float*)(b + L.snap);
     if (cudaMemset(h->err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "cudaMemset");
     if (p->storage == TPF_STORAGE_FP16) setup_tma<StoreF16>(h);
     else setup_tma<StoreF32>(h);
@@ -581,6 +644,7 @@ int tpflbm_init(tpflbm_t h, const float* phi, const float* ux, const float* uy, 
     // init reads the caller's buffers asynchronously: finish before returning
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     h->t = 0;
+    h->snap_t = -1;
     return TPF_OK;
 }
 
@@ -655,7 +719,7 @@ int tpflbm_set_state(tpflbm_t h, const float* f, const float* g, const float* hh
         for (int i = 0; i < 9; ++i)
             TPF_CUDA(h, cudaMemcpyAsync(h->stage + i * pl, srcs[k] + (long long)i * N, N * 4, cudaMemcpyDefault, h->stream));
         if (h->dp.storage == TPF_STORAGE_FP16) {
-            if (k != 1) k_lbe_ref<<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, h->ref[c]);
+            k_lbe_ref<<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, h->ref[c]);
             k_lbe_encode<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, (__half*)h->pop[c], h->ref[c]);
         } else {
             k_lbe_encode<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, k, h->stage, (float*)h->pop[c], h->ref[c]);
@@ -692,7 +756,7 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8])
 }
 
 int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void* pop, long long plane,
-                              const float* ref, const float* phiu, double out[8], void* stream)
+                              const void* ref, const float* phiu, double out[8], void* stream)
 {
     std::string why;
     int rc = validate(nx, ny, p, why);
@@ -701,7 +765,7 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void
     if (plane < (long long)nx * ny) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: plane must be >= nx * ny");
     if (plane > (1LL << 31) / 27) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: plane too large");
     const bool f16 = p->storage == TPF_STORAGE_FP16;
-    if (f16 && !ref) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: FP16 storage needs the reference planes");
+    if (f16 && !ref) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: FP16 storage needs the reference records");
 
     // the scratch's device address on the current device, looked up once per device
     static std::mutex mu;
@@ -730,9 +794,9 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void
     const int nb = (int)(b < kRedMaxBlocks ? b : kRedMaxBlocks);
     cudaStream_t s = (cudaStream_t)stream;
     if (f16)
-        k_reduce_partial<StoreF16><<<nb, kRedThreads, 0, s>>>(P, (const __half*)pop, ref, phiu, scratch);
+        k_reduce_partial<StoreF16><<<nb, kRedThreads, 0, s>>>(P, (const __half*)pop, (const RefT*)ref, phiu, scratch);
     else
-        k_reduce_partial<StoreF32><<<nb, kRedThreads, 0, s>>>(P, (const float*)pop, ref, phiu, scratch);
+        k_reduce_partial<StoreF32><<<nb, kRedThreads, 0, s>>>(P, (const float*)pop, (const RefT*)ref, phiu, scratch);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("k_reduce_partial: ") + cudaGetErrorString(e));
     double* res = scratch + kRedMaxBlocks * 8;
@@ -744,6 +808,40 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void
     double nf = 0.0;
     if (cudaMemcpy(&nf, res + 7, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess && nf > 0)
         return fail(nullptr, TPF_ERR_NONFINITE, "non-finite values in the state");
+    return TPF_OK;
+}
+
+int tpflbm_residual(tpflbm_t h, double dT, double out[3])
+{
+    if (!h || !out || !(dT > 0)) return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_residual needs out and dT > 0");
+    int rc = check_err(h);
+    if (rc) return rc;
+    const long long N = (long long)h->nx * h->ny;
+    long long b = (N + kRedThreads - 1) / kRedThreads;
+    const int nb = (int)(b < kRedMaxBlocks ? b : kRedMaxBlocks);
+    const int c = h->cur;
+    if (h->dp.storage == TPF_STORAGE_FP16)
+        k_residual_partial<StoreF16><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const __half*)h->pop[c], h->ref[c], h->phiu, h->snap, h->red);
+    else
+        k_residual_partial<StoreF32><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const float*)h->pop[c], h->ref[c], h->phiu, h->snap, h->red);
+    TPF_CUDA(h, cudaGetLastError());
+    double* res = h->red + kRedMaxBlocks * 8;
+    k_reduce_final<<<1, 32, 0, h->stream>>>(h->red, nb, res);
+    TPF_CUDA(h, cudaGetLastError());
+    double sums[8];
+    TPF_CUDA(h, cudaMemcpyAsync(sums, res, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+    const long long K = h->t - h->snap_t;
+    const bool first = h->snap_t < 0;
+    h->snap_t = h->t;
+    if (first || K <= 0) {
+        out[0] = out[1] = HUGE_VAL;
+        out[2] = 0;
+        return TPF_OK;
+    }
+    out[0] = sums[1] > 0 ? std::sqrt(sums[0]) / (K * std::sqrt(sums[1])) : (sums[0] > 0 ? HUGE_VAL : 0.0);
+    out[1] = std::sqrt(sums[2]) / (K * dT * std::sqrt((double)N));
+    out[2] = (double)K;
     return TPF_OK;
 }
 

@@ -59,6 +59,7 @@ SIGNATURES = {
     "tpflbm_set_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_diagnostics": ([_vp, _dp], _ip),
     "tpflbm_diagnostics_static": ([_ip, _ip, C.POINTER(Params), _vp, C.c_longlong, _vp, _vp, _vp, _vp], _ip),
+    "tpflbm_residual": ([_vp, C.c_double, _dp], _ip),
     "tpflbm_time": ([_vp], C.c_longlong),
     "tpflbm_destroy": ([_vp], None),
     "tpflbm_last_error": ([_vp], C.c_char_p),
@@ -218,6 +219,12 @@ class Lattice:
     def set_state(self, st):
         arrs = [np.ascontiguousarray(st[k], dtype=np.float32) for k in ("f", "g", "h", "phiu")]
         self._check(self.lib.tpflbm_set_state(self.h, *[_ptr(a) for a in arrs]))
+
+    def residual(self, dT: float):
+        """(r_u, r_T, K) of the steady-state residual (inf before the first snapshot)."""
+        out = (C.c_double * 3)()
+        self._check(self.lib.tpflbm_residual(self.h, float(dT), out))
+        return out[0], out[1], int(out[2])
 
     def diagnostics(self):
         out = (C.c_double * 8)()
