@@ -333,6 +333,41 @@ def bench_ensemble(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def bench_warmstart(args, rank, world, local_rank):
+    """Time to steady state of the 512 x 128 heated microchannel from the cold start
+    and from the trained network's prediction (committed weights), on held-out
+    instances, each on its own lattice and stream: steps to max(r_u, r_T) < 1e-7
+    with r checked every 1000 steps.  The warm time includes the network's input
+    upload, inference, phase-field projection and initialisation."""
+    import torch
+
+    from paper_2306_11320_gb300 import warmstart as WS
+
+    torch.cuda.set_device(local_rank)
+    net, norm, meta = WS.load(WS.WEIGHTS)
+    insts = WS.held_out(meta, args.instances)
+    tol, max_steps = 1e-7, 800_000
+    with ClockSampler(local_rank) as clk:
+        rows = WS.compare(net, norm, insts, tols=(tol,), max_steps=max_steps, log=lambda m: None)
+    if rank != 0:
+        return
+    summ = WS.summarize(rows, (tol,))
+    agg = summ["aggregate_1e-07"]
+    line = {
+        "metric": "time-to-steady speed-up (cold / learned warm start)", "value": agg["ratio"], "unit": "x",
+        "n_gpus": world, "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 LBM, bf16 network", "data": "synthetic",
+        "config": {"workload": "warmstart_512x128", "instances": len(insts), "tol": tol, "residual_K": WS.RESID_K,
+                   "max_steps": max_steps, "train_instances": meta["train"], "epochs": meta["epochs"]},
+        "aggregate": agg, "per_instance_median": summ["speedup_time_1e-07"],
+        "steps_median": summ["speedup_steps_1e-07"], "final_rel_l2_max": summ["final_rel_l2_max"],
+        "rows": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items() if k != "final_rel_l2"}
+                 for r in rows],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,9 +376,11 @@ def main():
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--workload", choices=("bubbles", "ensemble"), default="bubbles",
+    ap.add_argument("--workload", choices=("bubbles", "ensemble", "warmstart"), default="bubbles",
                     help="bubbles: the 2048x512 channel (the headline line); ensemble: the "
-                         "256-lattice parameter sweep through the batched launch")
+                         "256-lattice parameter sweep through the batched launch; warmstart: time to "
+                         "steady state, cold vs learned warm start, on held-out microchannels")
+    ap.add_argument("--instances", type=int, default=8, help="warmstart: held-out instances to time")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -360,6 +397,8 @@ def main():
     try:
         if args.workload == "ensemble":
             bench_ensemble(args, rank, world, local_rank)
+        elif args.workload == "warmstart":
+            bench_warmstart(args, rank, world, local_rank)
         else:
             bench_ours(args, rank, world, local_rank)
     finally:

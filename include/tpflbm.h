@@ -179,6 +179,27 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params *p, const void
  * the wall temperature difference).  Synchronises the stream. */
 int tpflbm_residual(tpflbm_t h, double dT, double out[3]);
 
+/* Mass-preserving projection of a predicted phase field (the warm start's output;
+ * the paper has no warm start).  phi_pred and phi_out are device [ny][nx] float
+ * arrays of this lattice's size (they may be the same array).  With the equilibrium
+ * profile phi = tanh(d / (sqrt(2) W)) (Sec. 2), the predicted signed distance of each
+ * node, a = d / (sqrt(2) W), is taken
+ *   mode TPF_PROJECT_ATANH:   as atanh(phi_pred) (phi_pred clipped to |phi| <= 1 - 1e-7);
+ *   mode TPF_PROJECT_CONTOUR: as (y_c(x) - y) / (sqrt(2) W), y_c(x) the lowest height
+ *       where phi_pred changes sign from positive to non-positive going up column x
+ *       (linear interpolation; heavy fluid below, an interface that is a graph over
+ *       x, as in the layered channel of Sec. 4.1; a column without a sign change
+ *       takes its node of least |phi_pred|).
+ * The call finds the uniform offset s for which sum_n tanh(a_n + s) equals target_sum
+ * (Newton's method on FP64 device sums, to 1e-12 per node) and writes
+ * phi_out = tanh(a + s) in float32.  *achieved (may be NULL) receives the FP64 sum
+ * before rounding.  Needs |target_sum| < nx * ny and a field with an interface;
+ * uses the lattice's staging memory (not its state) and synchronises its stream. */
+#define TPF_PROJECT_ATANH 0
+#define TPF_PROJECT_CONTOUR 1
+int tpflbm_project_phi(tpflbm_t h, const float *phi_pred, double target_sum, int mode, float *phi_out,
+                       double *achieved);
+
 /* Number of time steps taken since tpflbm_init. */
 long long tpflbm_time(tpflbm_t h);
 
@@ -217,6 +238,10 @@ int tpflbm_batch_step(tpflbm_batch_t b, long long nsteps);
 int tpflbm_batch_get_fields(tpflbm_batch_t b, int k, float *phi, float *ux, float *uy, float *p, float *T);
 /* tpflbm_diagnostics of every lattice: out[8 k + j], j as in tpflbm_diagnostics. */
 int tpflbm_batch_diagnostics(tpflbm_batch_t b, double *out);
+/* tpflbm_residual of every lattice: dT[k] the temperature scale of lattice k, out
+ * 3 doubles per lattice (n x 3).  Synchronises the batch's stream. */
+int tpflbm_batch_residual(tpflbm_batch_t b, const double *dT, double *out);
+
 /* The compiled tile shapes: *count of them, shape v is bx[v] x by[v] nodes (arrays of
  * at least *count entries, or NULL). */
 int tpflbm_batch_variants(int *count, int *bx, int *by);

@@ -72,6 +72,17 @@ int tpfnet_mse(const float *pred, const float *target, const float *wch, long lo
 int tpfnet_adam(float *p, const float *g, float *m, float *v, long long count, float lr, float b1, float b2,
                 float eps, int step, void *pb, void *stream);
 
+/* Planar fields to an interleaved tensor and back, with a per-channel affine map
+ * (scale, shift: host arrays of C floats, NULL = 1 and 0; 1 <= C <= 8) and optional
+ * base planes (device, same layout as the planar side, NULL = 0):
+ *   pack:   dst[p * Cd + c] = (src[c * plane + p] - base[c * plane + p]) * scale[c] + shift[c]
+ *           for c < C (float32 dst, or bf16 when dst_bf16 != 0; channels C..Cd-1 untouched);
+ *   unpack: dst[c * plane + p] = src[p * C + c] * scale[c] + shift[c] + base[c * plane + p]. */
+int tpfnet_pack(const float *src, const float *base, long long plane, int C, long long pixels, const float *scale,
+                const float *shift, void *dst, int Cd, int dst_bf16, void *stream);
+int tpfnet_unpack(const float *src, long long pixels, int C, const float *scale, const float *shift,
+                  const float *base, float *dst, long long plane, void *stream);
+
 /* y = bf16(x). */
 int tpfnet_to_bf16(const float *x, long long count, void *y, void *stream);
 

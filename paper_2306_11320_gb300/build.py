@@ -20,25 +20,39 @@ def sources():
 
 
 def _deps():
-    return sources() + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [
-        os.path.join(ROOT, "include", "tpflbm.h")]
+    return sources() + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + sorted(
+        glob.glob(os.path.join(HERE, "csrc", "*.h"))) + sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build_library(force: bool = False, verbose: bool = False, out: str | None = None, defines=()) -> str:
+    """Compile every csrc/*.cu (in parallel, one nvcc per file) and link the shared
+    library.  `out` and `defines` (-D flags) serve tuning builds beside the default."""
+    lib = out or LIB
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in _deps()):
-            return LIB
+            return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources()]
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+             *["-D" + d for d in defines]]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+        flags.insert(0, "-Xptxas=-v")
+    objs = [os.path.splitext(lib)[0] + "." + os.path.splitext(os.path.basename(s))[0] + ".%d.o" % os.getpid()
+            for s in sources()]
+    procs = [subprocess.Popen([nvcc, *flags, "-c", "-o", o, src]) for src, o in zip(sources(), objs)]
+    bad = [src for src, pr in zip(sources(), procs) if pr.wait() != 0]
+    try:
+        if bad:
+            raise RuntimeError("nvcc failed on %s" % ", ".join(os.path.basename(b) for b in bad))
+        tmp = lib + ".%d.tmp" % os.getpid()
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
+        os.replace(tmp, lib)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+    return lib
 
 
 if __name__ == "__main__":

@@ -335,6 +335,17 @@ int tpflbm_batch_diagnostics(tpflbm_batch_t b, double* out)
     return TPF_OK;
 }
 
+int tpflbm_batch_residual(tpflbm_batch_t b, const double* dT, double* out)
+{
+    if (!b || !dT || !out) return bfail(b, TPF_ERR_INVALID_ARG, "dT and out are required");
+    sync_instances(b);
+    for (int k = 0; k < b->n; ++k) {
+        int rc = tpflbm_residual(b->inst[k], dT[k], out + 3 * k);
+        if (rc != TPF_OK) return bfail(b, rc, tpflbm_last_error(b->inst[k]));
+    }
+    return TPF_OK;
+}
+
 int tpflbm_batch_variants(int* count, int* bx, int* by)
 {
     if (count) *count = kNumVariants;

@@ -407,9 +407,16 @@ struct PhiSmem {
     float irc[SN];
 };
 
-// CTAs per SM the TMA kernel is built for: shared memory allows 2 (FP32) or 3 (FP16)
+// CTAs per SM the TMA kernel is built for (shared memory allows 2 for FP32, 3 for
+// FP16; more CTAs means fewer registers per thread)
+#ifndef TPF_TMA_BLOCKS_F32
+#define TPF_TMA_BLOCKS_F32 2
+#endif
+#ifndef TPF_TMA_BLOCKS_F16
+#define TPF_TMA_BLOCKS_F16 3
+#endif
 template <class S>
-constexpr int kTmaMinBlocks = kRef<S> ? 3 : 2;
+constexpr int kTmaMinBlocks = kRef<S> ? TPF_TMA_BLOCKS_F16 : TPF_TMA_BLOCKS_F32;
 
 template <int BX, int BY, class S>
 __global__ void __launch_bounds__(BX * BY, kTmaMinBlocks<S>)

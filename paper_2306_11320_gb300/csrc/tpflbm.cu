@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kBX = 32, kBY = 8;
 constexpr int kMaxDevices = 64;
+constexpr long long kGraphSteps = 64;  // steps per replayed CUDA graph (even)
 
 // ------------------------------------------------------- auxiliary kernels
 
@@ -269,6 +270,73 @@ k_residual_partial(const DevParams P, const typename S::elem* __restrict__ A, co
         for (int w = 0; w < kRedThreads / 32; ++w) v += red[threadIdx.x][w];
         partial[blockIdx.x * 8 + threadIdx.x] = v;
     }
+}
+
+// Mass-preserving projection of a predicted phase field onto the equilibrium profile
+// phi = tanh(d / (sqrt(2) W)) (Sec. 2).  a_n = d_n / (sqrt(2) W) is the predicted
+// scaled signed distance of node n (k_project_dist*), offset by a uniform s chosen so
+// that sum phi matches a target.  Per block: sum phi(s) and its derivative
+// sum (1 - phi(s)^2).
+constexpr double kProjClip = 1.0 - 1e-7;
+// a_n = atanh(phi_hat_n) (phi_hat clipped into (-1, 1))
+__global__ void k_project_dist_atanh(const float* __restrict__ phat, long long N, float* __restrict__ a)
+{
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
+        a[n] = (float)atanh(fmin(fmax((double)phat[n], -kProjClip), kProjClip));
+}
+// a_n = (y_c(x) - y) / (sqrt(2) W) with y_c(x) the lowest zero crossing of phi_hat
+// in column x going up from positive to non-positive (linear interpolation between
+// the two nodes); a column without one uses the node of least |phi_hat|
+__global__ void k_project_dist_contour(const float* __restrict__ phat, int nx, int ny, float inv_sw, float* __restrict__ a)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    float yc = -1.f, best = 3.f;
+    int jbest = 0;
+    for (int j = 0; j + 1 < ny; ++j) {
+        const float p0 = phat[(long long)j * nx + x], p1 = phat[(long long)(j + 1) * nx + x];
+        if (p0 > 0.f && p1 <= 0.f) {
+            yc = (float)j + p0 / (p0 - p1);
+            break;
+        }
+        if (fabsf(p0) < best) {
+            best = fabsf(p0);
+            jbest = j;
+        }
+    }
+    if (yc < 0.f) yc = (float)jbest;
+    for (int j = 0; j < ny; ++j) a[(long long)j * nx + x] = (yc - (float)j) * inv_sw;
+}
+__global__ void __launch_bounds__(kRedThreads)
+k_project_partial(const float* __restrict__ a, long long N, double s, double* __restrict__ partial)
+{
+    double sa = 0.0, sb = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const double v = tanh((double)a[n] + s);
+        sa += v;
+        sb += 1.0 - v * v;
+    }
+    __shared__ double red[2][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = sa;
+        red[1][warp] = sb;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double v = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) v += red[threadIdx.x][w];
+        partial[blockIdx.x * 8 + threadIdx.x] = v;
+    }
+}
+__global__ void k_project_apply(const float* __restrict__ a, long long N, double s, float* __restrict__ out)
+{
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
+        out[n] = (float)tanh((double)a[n] + s);
 }
 
 }  // namespace
@@ -651,6 +719,30 @@ int tpflbm_init(tpflbm_t h, const float* phi, const float* ux, const float* uy, 
 int tpflbm_step(tpflbm_t h, long long nsteps)
 {
     if (!h || nsteps < 0) return TPF_ERR_INVALID_ARG;
+    // whole chunks from a CUDA graph when the stream can be captured (not the legacy
+    // default stream); kGraphSteps is even, so a chunk leaves the parity unchanged
+    while (h->stream && nsteps >= kGraphSteps) {
+        cudaGraphExec_t g = h->graph[h->cur];
+        if (!g) {
+            const int c0 = h->cur;
+            cudaGraph_t graph = nullptr;
+            TPF_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            for (long long s = 0; s < kGraphSteps; ++s) {
+                if (h->dp.storage == TPF_STORAGE_FP16) launch_step<StoreF16>(h);
+                else launch_step<StoreF32>(h);
+            }
+            cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+            h->cur = c0;
+            if (e != cudaSuccess) return fail(h, TPF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&h->graph[c0], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(h, TPF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            g = h->graph[c0];
+        }
+        TPF_CUDA(h, cudaGraphLaunch(g, h->stream));
+        nsteps -= kGraphSteps;
+        h->t += kGraphSteps;
+    }
     for (long long s = 0; s < nsteps; ++s) {
         if (h->dp.storage == TPF_STORAGE_FP16) launch_step<StoreF16>(h);
         else launch_step<StoreF32>(h);
@@ -845,11 +937,61 @@ int tpflbm_residual(tpflbm_t h, double dT, double out[3])
     return TPF_OK;
 }
 
+int tpflbm_project_phi(tpflbm_t h, const float* phi_pred, double target_sum, int mode, float* phi_out,
+                       double* achieved)
+{
+    if (!h || !phi_pred || !phi_out) return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_project_phi needs phi_pred and phi_out");
+    if (mode != TPF_PROJECT_ATANH && mode != TPF_PROJECT_CONTOUR)
+        return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_project_phi: unknown mode");
+    const long long N = (long long)h->nx * h->ny;
+    if (!(std::fabs(target_sum) < (double)N)) return fail(h, TPF_ERR_INVALID_ARG, "target sum must lie strictly inside (-N, N)");
+    // scaled distances in the last staging plane
+    float* a = h->stage + 8 * h->dp.plane;
+    if (mode == TPF_PROJECT_ATANH) {
+        k_project_dist_atanh<<<grid_1d(N), 256, 0, h->stream>>>(phi_pred, N, a);
+    } else {
+        const float inv_sw = (float)(1.0 / (std::sqrt(2.0) * h->hp.W));
+        k_project_dist_contour<<<(h->nx + 127) / 128, 128, 0, h->stream>>>(phi_pred, h->nx, h->ny, inv_sw, a);
+    }
+    TPF_CUDA(h, cudaGetLastError());
+    const long long b = (N + kRedThreads - 1) / kRedThreads;
+    const int nb = (int)(b < kRedMaxBlocks ? b : kRedMaxBlocks);
+    double* res = h->red + kRedMaxBlocks * 8;
+    double s = 0.0, sums[2] = {0.0, 0.0};
+    const double tol = 1e-12 * (double)N;
+    // Newton on S(s) = sum tanh(a_n + s), increasing in s
+    int it = 0;
+    for (; it < 100; ++it) {
+        k_project_partial<<<nb, kRedThreads, 0, h->stream>>>(a, N, s, h->red);
+        TPF_CUDA(h, cudaGetLastError());
+        k_reduce_final<<<1, 32, 0, h->stream>>>(h->red, nb, res);
+        TPF_CUDA(h, cudaGetLastError());
+        TPF_CUDA(h, cudaMemcpyAsync(sums, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+        const double r = sums[0] - target_sum;
+        if (!std::isfinite(r)) return fail(h, TPF_ERR_NONFINITE, "tpflbm_project_phi: non-finite predicted phase field");
+        if (std::fabs(r) <= tol) break;
+        if (!(sums[1] > 0.0)) return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_project_phi: the field has no interface to move");
+        double step = r / sums[1];
+        if (step > 2.0) step = 2.0;  // keep the iterate inside tanh's useful range
+        if (step < -2.0) step = -2.0;
+        s -= step;
+    }
+    if (it == 100) return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_project_phi: no convergence");
+    k_project_apply<<<grid_1d(N), 256, 0, h->stream>>>(a, N, s, phi_out);
+    TPF_CUDA(h, cudaGetLastError());
+    TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (achieved) *achieved = sums[0];
+    return TPF_OK;
+}
+
 long long tpflbm_time(tpflbm_t h) { return h ? h->t : -1; }
 
 void tpflbm_destroy(tpflbm_t h)
 {
     if (!h) return;
+    for (int c = 0; c < 2; ++c)
+        if (h->graph[c]) cudaGraphExecDestroy(h->graph[c]);
     if (h->owns && h->ws) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->ws);

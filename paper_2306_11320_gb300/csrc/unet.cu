@@ -373,6 +373,33 @@ __global__ void k_to_bf16(const float* __restrict__ x, long long count, bf16* __
         y[k] = __float2bfloat16_rn(x[k]);
 }
 
+// planar float fields <-> interleaved NHWC tensors, with a per-channel affine map
+constexpr int kMaxPackC = 8;
+struct Affine {
+    float scale[kMaxPackC], shift[kMaxPackC];
+};
+__global__ void k_pack(const float* __restrict__ src, const float* __restrict__ base, long long plane, int C,
+                       long long pixels, Affine a, void* __restrict__ dst, int Cd, int bf)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pixels * C; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        const long long p = k / C;
+        const float d = src[c * plane + p] - (base ? base[c * plane + p] : 0.f);
+        const float v = fmaf(d, a.scale[c], a.shift[c]);
+        if (bf) ((bf16*)dst)[p * Cd + c] = __float2bfloat16_rn(v);
+        else ((float*)dst)[p * Cd + c] = v;
+    }
+}
+__global__ void k_unpack(const float* __restrict__ src, long long pixels, int C, Affine a, const float* __restrict__ base,
+                         float* __restrict__ dst, long long plane)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < pixels * C; k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k % C);
+        const long long p = k / C;
+        dst[c * plane + p] = fmaf(src[k], a.scale[c], a.shift[c]) + (base ? base[c * plane + p] : 0.f);
+    }
+}
+
 int grid_of(long long count)
 {
     long long b = (count + 255) / 256;
@@ -509,6 +536,35 @@ int tpfnet_adam(float* p, const float* g, float* m, float* v, long long count, f
 {
     const float c1 = 1.f / (1.f - powf(b1, (float)step)), c2 = 1.f / (1.f - powf(b2, (float)step));
     k_adam<<<grid_of(count), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, count, lr, b1, b2, eps, c1, c2, (bf16*)pb);
+    return status(cudaGetLastError());
+}
+
+static int affine_of(int C, const float* scale, const float* shift, Affine* a)
+{
+    if (C < 1 || C > kMaxPackC) return TPF_ERR_INVALID_ARG;
+    for (int c = 0; c < C; ++c) {
+        a->scale[c] = scale ? scale[c] : 1.f;
+        a->shift[c] = shift ? shift[c] : 0.f;
+    }
+    return TPF_OK;
+}
+
+int tpfnet_pack(const float* src, const float* base, long long plane, int C, long long pixels, const float* scale,
+                const float* shift, void* dst, int Cd, int dst_bf16, void* stream)
+{
+    Affine a;
+    if (!src || !dst || Cd < C || plane < pixels || affine_of(C, scale, shift, &a)) return TPF_ERR_INVALID_ARG;
+    k_pack<<<grid_of(pixels * C), 256, 0, (cudaStream_t)stream>>>(src, base, plane, C, pixels, a, dst, Cd,
+                                                                 dst_bf16 ? 1 : 0);
+    return status(cudaGetLastError());
+}
+
+int tpfnet_unpack(const float* src, long long pixels, int C, const float* scale, const float* shift, const float* base,
+                  float* dst, long long plane, void* stream)
+{
+    Affine a;
+    if (!src || !dst || plane < pixels || affine_of(C, scale, shift, &a)) return TPF_ERR_INVALID_ARG;
+    k_unpack<<<grid_of(pixels * C), 256, 0, (cudaStream_t)stream>>>(src, pixels, C, a, base, dst, plane);
     return status(cudaGetLastError());
 }
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "tpflbm_diagnostics": ([_vp, _dp], _ip),
     "tpflbm_diagnostics_static": ([_ip, _ip, C.POINTER(Params), _vp, C.c_longlong, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_residual": ([_vp, C.c_double, _dp], _ip),
+    "tpflbm_project_phi": ([_vp, _vp, C.c_double, _ip, _vp, _dp], _ip),
     "tpflbm_time": ([_vp], C.c_longlong),
     "tpflbm_destroy": ([_vp], None),
     "tpflbm_last_error": ([_vp], C.c_char_p),
@@ -71,6 +72,7 @@ SIGNATURES = {
     "tpflbm_batch_step": ([_vp, C.c_longlong], _ip),
     "tpflbm_batch_get_fields": ([_vp, _ip, _vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_batch_diagnostics": ([_vp, _dp], _ip),
+    "tpflbm_batch_residual": ([_vp, _dp, _dp], _ip),
     "tpflbm_batch_variants": ([C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], _ip),
     "tpflbm_batch_set_variant": ([_vp, _ip], _ip),
     "tpflbm_batch_tune": ([_vp, _ip, _dp, C.POINTER(C.c_int)], _ip),
@@ -226,6 +228,19 @@ class Lattice:
         self._check(self.lib.tpflbm_residual(self.h, float(dT), out))
         return out[0], out[1], int(out[2])
 
+    def project_phi(self, phi_pred, target_sum: float, mode: int = 1, out=None):
+        """Mass-preserving projection of a predicted phase field (a float32 CUDA tensor
+        of shape (ny, nx)) onto the tanh profile (mode 1: about each column's zero
+        crossing; 0: through atanh); returns (phi, achieved FP64 sum)."""
+        t = self.torch
+        assert phi_pred.is_cuda and phi_pred.dtype == t.float32 and tuple(phi_pred.shape) == (self.ny, self.nx)
+        phi_pred = phi_pred.contiguous()
+        out = t.empty_like(phi_pred) if out is None else out
+        got = C.c_double()
+        self._check(self.lib.tpflbm_project_phi(self.h, C.c_void_p(phi_pred.data_ptr()), float(target_sum), int(mode),
+                                                C.c_void_p(out.data_ptr()), C.byref(got)))
+        return out, got.value
+
     def diagnostics(self):
         out = (C.c_double * 8)()
         rc = self.lib.tpflbm_diagnostics(self.h, out)
@@ -297,6 +312,13 @@ class Batch:
         out = [np.empty((ny, nx), dtype=np.float32) for _ in range(5)]
         self._check(self.lib.tpflbm_batch_get_fields(self.h, int(k), *[_ptr(a) for a in out]))
         return dict(zip(("phi", "ux", "uy", "p", "T"), out))
+
+    def residual(self, dT):
+        """(n, 3) array of (r_u, r_T, K) per lattice; dT a scalar or one per lattice."""
+        d = np.broadcast_to(np.asarray(dT, dtype=np.float64), (self.n,)).copy()
+        out = (C.c_double * (3 * self.n))()
+        self._check(self.lib.tpflbm_batch_residual(self.h, d.ctypes.data_as(C.POINTER(C.c_double)), out))
+        return np.array(out[:]).reshape(self.n, 3)
 
     def diagnostics(self):
         out = (C.c_double * (8 * self.n))()

@@ -35,6 +35,8 @@ SIGNATURES = {
     "tpfnet_mse": [_vp, _vp, _vp, _ll, _ip, _vp, _vp, _vp],
     "tpfnet_adam": [_vp, _vp, _vp, _vp, _ll, _fl, _fl, _fl, _fl, _ip, _vp, _vp],
     "tpfnet_to_bf16": [_vp, _ll, _vp, _vp],
+    "tpfnet_pack": [_vp, _vp, _ll, _ip, _ll, _vp, _vp, _vp, _ip, _ip, _vp],
+    "tpfnet_unpack": [_vp, _ll, _ip, _vp, _vp, _vp, _vp, _ll, _vp],
 }
 
 PAD = 32  # channel granularity of the convolution kernels

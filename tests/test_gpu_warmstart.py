@@ -1,0 +1,85 @@
+"""Warm-start pieces through the C-ABI (needs a GB300): the mass-preserving phase-field
+projection against its FP64 definition, and the planar <-> interleaved packing."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import warmstart_ref as R
+from paper_2306_11320_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _pred(nx, ny, W, seed):
+    """A network-like prediction: a wavy layer with the wrong bulk value and noise."""
+    rng = np.random.default_rng(seed)
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    yc = 0.45 * ny + 2.0 * np.sin(2 * np.pi * np.arange(nx) / nx + 0.3)
+    clean = np.tanh((yc[None, :] - y) / (np.sqrt(2.0) * W))
+    return (0.93 * clean + 0.02 * rng.standard_normal(clean.shape)).astype(np.float32)
+
+
+@pytest.mark.parametrize("mode,name", [(1, "contour"), (0, "atanh")])
+@pytest.mark.parametrize("nx,ny", [(128, 32), (200, 56)])
+def test_projection_matches_definition(mode, name, nx, ny):
+    from paper_2306_11320_gb300.tpflbm import Lattice
+
+    p, f, _ = WL.microchannel(nx=nx, ny=ny)
+    lat = Lattice(nx, ny, p)
+    pred = _pred(nx, ny, p["W"], seed=nx + mode)
+    target = float(f["phi"].astype(np.float32).astype(np.float64).sum())
+    out, got = lat.project_phi(torch.from_numpy(pred).cuda(), target, mode=mode)
+    ref, s, ref_sum = R.project_phi(pred.astype(np.float64), p["W"], target, name)
+    assert abs(got - target) <= 1e-12 * nx * ny
+    # the device keeps the scaled distances in float32: phi agrees to ~1e-6
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-5
+    assert abs(out.cpu().numpy().astype(np.float64).sum() - target) <= 1e-6 * nx * ny
+
+
+def test_pack_unpack_with_base():
+    from paper_2306_11320_gb300.unet import net_library
+
+    lib = net_library()
+    rng = np.random.default_rng(3)
+    P, Cc, Cd = 777, 5, 8
+    src = rng.standard_normal((Cc, P)).astype(np.float32)
+    base = rng.standard_normal((Cc, P)).astype(np.float32)
+    scale = np.array([1.0, 2.0, 0.5, -1.0, 4.0], dtype=np.float32)
+    shift = np.array([0.0, 1.0, -2.0, 0.25, 3.0], dtype=np.float32)
+    s_, b_ = torch.from_numpy(src).cuda(), torch.from_numpy(base).cuda()
+    dst = torch.full((P, Cd), 7.0, dtype=torch.float32, device="cuda")
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sc, sh = (C.c_float * Cc)(*scale), (C.c_float * Cc)(*shift)
+    assert lib.tpfnet_pack(C.c_void_p(s_.data_ptr()), C.c_void_p(b_.data_ptr()), P, Cc, P, sc, sh,
+                           C.c_void_p(dst.data_ptr()), Cd, 0, st) == 0
+    d = dst.cpu().numpy()
+    ref = ((src - base) * scale[:, None] + shift[:, None]).T
+    assert np.allclose(d[:, :Cc], ref, rtol=1e-6, atol=1e-6) and np.all(d[:, Cc:] == 7.0)
+    back = torch.empty((Cc, P), dtype=torch.float32, device="cuda")
+    inv = (C.c_float * Cc)(*(1.0 / scale))
+    ish = (C.c_float * Cc)(*(-shift / scale))
+    # unpack reads an interleaved tensor with exactly Cc channels
+    dense = torch.from_numpy(np.ascontiguousarray(d[:, :Cc])).cuda()
+    assert lib.tpfnet_unpack(C.c_void_p(dense.data_ptr()), P, Cc, inv, ish, C.c_void_p(b_.data_ptr()),
+                             C.c_void_p(back.data_ptr()), P, st) == 0
+    assert np.allclose(back.cpu().numpy(), src, rtol=1e-5, atol=1e-5)
+
+
+def test_trained_network_shortens_time_to_steady():
+    """The committed network on two held-out channels with k = 1 (the slow ones): the
+    warm start reaches r < 1e-7 in less than half the cold start's steps, and both
+    runs end in the same state to within the slow-mode drift the residual allows."""
+    from paper_2306_11320_gb300 import warmstart as WS
+
+    net, norm, meta = WS.load(WS.WEIGHTS)
+    insts = [i for i in WS.held_out(meta) if i["k"] == 1][:2]
+    assert len(insts) == 2
+    rows = WS.compare(net, norm, insts, tols=(1e-7,), max_steps=800_000, log=lambda m: None)
+    for r in rows:
+        assert r["warm_steps_1e-07"] is not None
+        cold = r["cold_steps_1e-07"] or 800_000
+        assert 2 * r["warm_steps_1e-07"] < cold, r
+        assert r["final_rel_l2"]["T"] < 1e-3 and r["final_rel_l2"]["phi"] < 1e-3, r
