@@ -34,8 +34,8 @@ NX, NY = 2048, 512
 WORKLOAD = "bubbles_2048x512"
 # algorithmic bytes per lattice update: every population read once and written once
 # (27 x 2 x element size) plus the previous (phi u) read and written (2 x 2 x 4 B);
-# FP16 storage adds the float32 references phi, T, p of each node (read and written)
-ALG_BYTES = {"fp32": 27 * 2 * 4 + 16, "fp16": 27 * 2 * 2 + 16 + 24}
+# FP16 storage adds each node's three 8-byte reference records (read and written)
+ALG_BYTES = {"fp32": 27 * 2 * 4 + 16, "fp16": 27 * 2 * 2 + 16 + 48}
 CPU_SAMPLE_SECONDS = 15.0
 
 

@@ -64,14 +64,15 @@ typedef struct tpflbm *tpflbm_t;
  *       T_top(x) = T_top + T_top_slope x (Sec. 4.1-4.3); 1: periodic in y.
  *   storage: TPF_STORAGE_FP32 or TPF_STORAGE_FP16.  With FP16 a population q_i of
  *       LBE k is stored in float16 as s_k (q_i - r_i), its deviation from a
- *       reference that the node it streamed from leaves for it: the rest
+ *       reference that the node which wrote it (the node it streamed from; for a
+ *       population reflected at a boundary the node itself; for f, h entering through
+ *       the outflow the last-column node that copied it) leaves for it: the rest
  *       equilibrium plus the first-order term of what that node emitted,
- *       r_i = w_i (phi + c_i . J_f / cs2) for f, w_i (T + c_i . J_h / cs2) for h
- *       (J the first moment of the post-collision populations; the J term is
- *       dropped for populations reflected at a boundary), w_i p / cs2 (i != 0) and
- *       (w_0 - 1) p / cs2 (i = 0) for g.  Each node keeps two records of four
- *       halves for this: (phi, J_fx/cs2, J_fy/cs2, p/cs2) and (T, J_hx/cs2,
- *       J_hy/cs2, 0).
+ *       r_i = w_i (phi + c_i . J_f / cs2) for f, w_i (T + c_i . J_h / cs2) for h,
+ *       wg_i p / cs2 + w_i c_i . J_g / cs2 for g (wg_0 = w_0 - 1, wg_i = w_i), with J
+ *       the first moment of the post-collision populations.  Each node keeps one
+ *       8-byte record per LBE for this: the zeroth moment (phi, p / cs2, T) in float32
+ *       and J / cs2 as two halves.
  *       s_k are powers of two, fp16_scale_f/g/h (0 selects the defaults 1024, 1024,
  *       64).  All arithmetic stays float32.
  */
@@ -148,9 +149,9 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8]);
  *         elements each, [ny][nx] inside a plane; float32, or float16 encoded as in
  *         tpflbm_params.storage when p->storage is TPF_STORAGE_FP16.
  *   plane elements per plane, >= nx * ny.
- *   ref   FP16 storage only: the reference records of the previous step, two
- *         planes of `plane` 8-byte records (four halves each, see
- *         tpflbm_params.storage); NULL for FP32.
+ *   ref   FP16 storage only: the reference records of the previous step, three
+ *         planes (f, g, h) of `plane` 8-byte records (float32 zeroth moment, then
+ *         two halves, see tpflbm_params.storage); NULL for FP32.
  *   phiu  device pointer, 2 float planes of `plane` elements ((phi u) of the
  *         previous step).
  *   out   8 doubles, host or device memory; same meaning as tpflbm_diagnostics.

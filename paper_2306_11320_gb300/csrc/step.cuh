@@ -14,63 +14,67 @@
 namespace tpf {
 
 // FP16 storage keeps the scaled deviation s_k (q_i - r_i) of each population from a
-// reference r_i built from a record that the population's writer (its source node
-// y - c_i, wrapped when periodic) leaves for the next step:
+// reference r_i built from a record that the population's writer leaves for the next
+// step:
 //   f: r_i = w_i (phi + c_i . J_f / cs2)      h: r_i = w_i (T + c_i . J_h / cs2)
-//   g: r_i = w_i p / cs2 (i != 0), (w_0 - 1) p / cs2 (i = 0)
-// with phi, T, p the writer's moments and J_f, J_h the first moments of its
-// post-collision f and h, i.e. the rest equilibrium plus the first-order Hermite term
+//   g: r_i = wg_i p / cs2 + w_i c_i . J_g / cs2   (wg_0 = w_0 - 1, wg_i = w_i)
+// with phi, T, p the writer's moments and J_f, J_g, J_h the first moments of its
+// post-collision f, g, h, i.e. the rest equilibrium plus the first-order Hermite term
 // of what it emitted, so that only the higher-order non-equilibrium part is
-// quantised.  A population whose source lies outside the fluid (reflected at a wall,
-// the inlet or the outflow plane) was written by the node that holds it, and its
-// reference drops the first-moment term.  Each record is four halves (phi, J_fx/cs2,
-// J_fy/cs2, p/cs2) and (T, J_hx/cs2, J_hy/cs2, 0); the writer encodes against the
-// rounded record, so encoder and decoder see the same reference bit for bit.
+// quantised.  The writer of population i at y is the node it streamed from, y - c_i
+// (wrapped when periodic), except where y - c_i lies outside the fluid: a population
+// reflected at a wall or at the inlet (and g reflected at the outflow) was written by
+// y itself, and f, h entering through the outflow are the copies that the last
+// column's node y - c_iy (same column) made of its own populations.  A record is one
+// 8-byte word per LBE and node: the zeroth moment in float32 and J / cs2 as two
+// halves; the writer encodes against the rounded record, so encoder and decoder see
+// the same reference bit for bit.
 template <class S>
 constexpr bool kRef = std::is_same<S, StoreF16>::value;
 
-using RefT = uint2;  // one reference record: four halves
+using RefT = uint2;  // one reference record: float32 zeroth moment, half2 first moment / cs2
+constexpr int kRecF = 0, kRecG = 1, kRecH = 2;  // record planes
 
 struct RefVals {
-    float m0, jx, jy, w;
+    float m0, jx, jy;
 };
 __device__ __forceinline__ RefVals ref_unpack(RefT q)
 {
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-    return {a.x, a.y, b.x, b.y};
+    const float2 j = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    return {__uint_as_float(q.x), j.x, j.y};
 }
-// rounds (m0, jx, jy, w) to halves; r receives the rounded values
-__device__ __forceinline__ RefT ref_pack(float m0, float jx, float jy, float w, RefVals& r)
+// keeps m0, rounds (jx, jy) to halves; r receives the values the decoder will see
+__device__ __forceinline__ RefT ref_pack(float m0, float jx, float jy, RefVals& r)
 {
-    const __half2 a = __floats2half2_rn(m0, jx), b = __floats2half2_rn(jy, w);
-    const float2 fa = __half22float2(a), fb = __half22float2(b);
-    r = {fa.x, fa.y, fb.x, fb.y};
+    const __half2 j = __floats2half2_rn(jx, jy);
+    const float2 fj = __half22float2(j);
+    r = {m0, fj.x, fj.y};
     RefT q;
-    q.x = *reinterpret_cast<const uint32_t*>(&a);
-    q.y = *reinterpret_cast<const uint32_t*>(&b);
+    q.x = __float_as_uint(m0);
+    q.y = *reinterpret_cast<const uint32_t*>(&j);
     return q;
 }
-__device__ __forceinline__ float half_round(float v) { return __half2float(__float2half_rn(v)); }
 
 // reference of population i of f or h from its writer's record
-__device__ __forceinline__ float ref_pop(int i, const RefVals& r, bool self)
+__device__ __forceinline__ float ref_pop(int i, const RefVals& r)
 {
-    return self ? wq(i) * r.m0 : wq(i) * (r.m0 + (float)cx(i) * r.jx + (float)cy(i) * r.jy);
+    return wq(i) * (r.m0 + (float)cx(i) * r.jx + (float)cy(i) * r.jy);
+}
+// reference of population i of g (r.m0 = p / cs2)
+__device__ __forceinline__ float ref_g(int i, const RefVals& r)
+{
+    return fmaf(wg(i), r.m0, wq(i) * ((float)cx(i) * r.jx + (float)cy(i) * r.jy));
 }
 
-// node whose record is the FP16 reference of population i at (x, y); self is set when
-// y - c_i lies outside the fluid (the node itself wrote the population)
-__device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int i, bool& self)
+// node that wrote population i at (x, y), whose record is its FP16 reference (for the
+// g LBE when g_lbe: the outflow reflects g at the node itself)
+__device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int i, bool g_lbe)
 {
     int sx = x - cx(i), sy = y - cy(i);
     if (P.bc_x == 0) sx = wrap(sx, P.nx);
     if (P.bc_y == 1) sy = wrap(sy, P.ny);
-    self = sx < 0 || sx >= P.nx || sy < 0 || sy >= P.ny;
-    if (self) {
-        sx = x;
-        sy = y;
-    }
+    if (sy < 0 || sy >= P.ny || sx < 0 || (sx >= P.nx && g_lbe)) return y * P.nx + x;
+    if (sx >= P.nx) return sy * P.nx + (P.nx - 1);  // outflow copy made by (nx - 1, sy)
     return sy * P.nx + sx;
 }
 
@@ -86,13 +90,10 @@ __device__ __forceinline__ void load_node(const DevParams& P, const typename S::
     for (int i = 0; i < 9; ++i) {
         float rf = 0.f, rg = 0.f, rh = 0.f;
         if constexpr (kRef<S>) {
-            bool self;
-            const int s = ref_source(P, x, y, i, self);
-            const RefVals a = ref_unpack(ref[s]);
-            const RefVals b = ref_unpack(ref[pl + s]);
-            rf = ref_pop(i, a, self);
-            rg = wg(i) * a.w;
-            rh = ref_pop(i, b, self);
+            const int s = ref_source(P, x, y, i, false);
+            rf = ref_pop(i, ref_unpack(ref[kRecF * pl + s]));
+            rh = ref_pop(i, ref_unpack(ref[kRecH * pl + s]));
+            if constexpr (WANT_G) rg = ref_g(i, ref_unpack(ref[kRecG * pl + ref_source(P, x, y, i, true)]));
         }
         f[i] = S::ld(A + i * pl, n, P.is_f, rf);
         if constexpr (WANT_G) g[i] = S::ld(A + (9 + i) * pl, n, P.is_g, rg);
@@ -111,46 +112,47 @@ struct RingSmem {
 };
 
 // Collide the node's populations and push them to their destinations, with every
-// boundary rule; for FP16 also leave the node's reference records in refB.
-// hold(i, k) and irc(k) give the pre-collision h_i and 1/(rho c_p) of the node in
-// ring slot k; phiR(k), TR(k) its phi and T.
-template <class S, int SX, class HOLD, class IRC, class PHIR, class TR>
+// boundary rule; for FP16 also leave the node's reference records in refB (every
+// population this node writes is encoded against them).  hold(i, k) and irc(k) give
+// the pre-collision h_i and 1/(rho c_p) of the node in ring slot k.
+template <class S, int SX, class HOLD, class IRC>
 __device__ __forceinline__ void collide_push(const DevParams& P, typename S::elem* __restrict__ B,
                                              RefT* __restrict__ refB, int x, int y, int kown, bool interior,
-                                             const Macro& m, float* f, float* g, float* h, HOLD hold, IRC irc,
-                                             PHIR phiR, TR TR_)
+                                             const Macro& m, float* f, float* g, float* h, HOLD hold, IRC irc)
 {
     const long long pl = P.plane;
     const int n = y * P.nx + x;
     node_collide(P, m, f, g, h);
-    // FP16 reference records of what this node emits (rounded values in rf, rh)
-    RefVals rf{0.f, 0.f, 0.f, 0.f}, rh{0.f, 0.f, 0.f, 0.f};
+    // FP16 reference records of what this node emits (as the decoder sees them)
+    RefVals rf{0.f, 0.f, 0.f}, rgv{0.f, 0.f, 0.f}, rh{0.f, 0.f, 0.f};
     if constexpr (kRef<S>) {
-        float jfx = 0.f, jfy = 0.f, jhx = 0.f, jhy = 0.f;
+        float jfx = 0.f, jfy = 0.f, jgx = 0.f, jgy = 0.f, jhx = 0.f, jhy = 0.f;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (cx(i) != 0) {
                 jfx += (float)cx(i) * f[i];
+                jgx += (float)cx(i) * g[i];
                 jhx += (float)cx(i) * h[i];
             }
             if (cy(i) != 0) {
                 jfy += (float)cy(i) * f[i];
+                jgy += (float)cy(i) * g[i];
                 jhy += (float)cy(i) * h[i];
             }
         }
-        refB[n] = ref_pack(m.phi, jfx * kInvCs2, jfy * kInvCs2, m.p * kInvCs2, rf);
-        refB[pl + n] = ref_pack(m.T, jhx * kInvCs2, jhy * kInvCs2, 0.f, rh);
+        refB[kRecF * pl + n] = ref_pack(m.phi, jfx * kInvCs2, jfy * kInvCs2, rf);
+        refB[kRecG * pl + n] = ref_pack(m.p * kInvCs2, jgx * kInvCs2, jgy * kInvCs2, rgv);
+        refB[kRecH * pl + n] = ref_pack(m.T, jhx * kInvCs2, jhy * kInvCs2, rh);
     }
-    const float rg = rf.w;
     if (interior) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int d = n + cy(i) * P.nx + cx(i);
             const int kd = kown + cy(i) * SX + cx(i);
-            S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf, false));
-            S::st(B + (9 + i) * pl, d, g[i], P.s_g, wg(i) * rg);
+            S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf));
+            S::st(B + (9 + i) * pl, d, g[i], P.s_g, ref_g(i, rgv));
             const float ho = hold(i, kd);
-            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh, false));
+            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh));
         }
         return;
     }
@@ -168,47 +170,45 @@ __device__ __forceinline__ void collide_push(const DevParams& P, typename S::ele
             // temperature at the link's crossing point
             const float xc = (float)x + 0.5f * cx(i);
             const float Tw = (cy(i) < 0) ? T_wall_bottom(P, xc) : T_wall_top(P, xc);
-            S::st(B + o * pl, n, f[i], P.s_f, ref_pop(o, rf, true));
-            S::st(B + (9 + o) * pl, n, g[i], P.s_g, wg(o) * rg);
+            S::st(B + o * pl, n, f[i], P.s_f, ref_pop(o, rf));
+            S::st(B + (9 + o) * pl, n, g[i], P.s_g, ref_g(o, rgv));
             const float ho = hold(o, kown);
             const float hin = -h[i] + 2.f * wq(o) * Tw;
-            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, ref_pop(o, rh, true));
+            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, ref_pop(o, rh));
         } else if (out_x && dx < 0) {
             // velocity inlet: bounce-back carrying the inlet momentum and phi_in
             const float ycr = (float)y + 0.5f + 0.5f * cy(i);
             const float cu = cx(o) * u_inlet(P, ycr);
-            S::st(B + o * pl, n, f[i] + 2.f * wq(o) * P.phi_in * cu * kInvCs2, P.s_f, ref_pop(o, rf, true));
-            S::st(B + (9 + o) * pl, n, g[i] + 2.f * wq(o) * m.rho * cu * kInvCs2, P.s_g, wg(o) * rg);
+            S::st(B + o * pl, n, f[i] + 2.f * wq(o) * P.phi_in * cu * kInvCs2, P.s_f, ref_pop(o, rf));
+            S::st(B + (9 + o) * pl, n, g[i] + 2.f * wq(o) * m.rho * cu * kInvCs2, P.s_g, ref_g(o, rgv));
             const float ho = hold(o, kown);
             const float hin = -h[i] + 2.f * wq(o) * P.T_in;
-            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, ref_pop(o, rh, true));
+            S::st(B + (18 + o) * pl, n, fmaf(hin - ho, irc_own, ho), P.s_h, ref_pop(o, rh));
         } else if (out_x) {
             // outflow: pressure anti-bounce-back of g (f and h arrive by the copy below)
             const float cu = cx(o) * m.ux + cy(o) * m.uy;
             const float sym = P.p_out * kInvCs2 +
                               m.rho * (0.5f * cu * cu * kInvCs2 * kInvCs2 - 0.5f * (m.ux * m.ux + m.uy * m.uy) * kInvCs2);
-            S::st(B + (9 + o) * pl, n, -g[i] + 2.f * wq(o) * sym, P.s_g, wg(o) * rg);
+            S::st(B + (9 + o) * pl, n, -g[i] + 2.f * wq(o) * sym, P.s_g, ref_g(o, rgv));
         } else {
             const int d = dy * P.nx + dx;
             const int kd = kown + cy(i) * SX + cx(i);
-            S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf, false));
-            S::st(B + (9 + i) * pl, d, g[i], P.s_g, wg(i) * rg);
+            S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf));
+            S::st(B + (9 + i) * pl, d, g[i], P.s_g, ref_g(i, rgv));
             const float ho = hold(i, kd);
-            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh, false));
+            S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh));
         }
         // zero-gradient outflow of f and h: the ghost column beyond x = nx-1 carries the
-        // post-collision populations of the last column.  The destination decodes them
-        // with the zeroth moment of its own record (their source lies outside), so
-        // encode with its rounded phi and T.
+        // post-collision populations of the last column (this node wrote them, so they
+        // are encoded against its own records).
         if (P.bc_x == 1 && x == P.nx - 1 && cx(i) < 0) {
             const int ey = y + cy(i);
             if (ey >= 0 && ey < P.ny) {
                 const int d = ey * P.nx + x;
                 const int kd = kown + cy(i) * SX;
-                S::st(B + i * pl, d, f[i], P.s_f, kRef<S> ? wq(i) * half_round(phiR(kd)) : 0.f);
+                S::st(B + i * pl, d, f[i], P.s_f, ref_pop(i, rf));
                 const float ho = hold(i, kd);
-                S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h,
-                      kRef<S> ? wq(i) * half_round(TR_(kd)) : 0.f);
+                S::st(B + (18 + i) * pl, d, fmaf(h[i] - ho, irc(kd), ho), P.s_h, ref_pop(i, rh));
             }
         }
     }
@@ -310,7 +310,7 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
         phiu[pl + n] = m.phi * m.uy;
         collide_push<S, SX>(
             P, B, refB, x, y, kown, interior, m, f, g, h, [&](int i, int k) { return sm.h[i][k]; },
-            [&](int k) { return sm.irc[k]; }, [&](int k) { return sm.phi[k]; }, [&](int k) { return sm.T[k]; });
+            [&](int k) { return sm.irc[k]; });
     }
     __syncthreads();  // the caller may reuse sm for the next tile
 }
@@ -331,7 +331,7 @@ k_step_general(const DevParams P, const typename S::elem* __restrict__ A, typena
 // tiles through the general path.  For a TMA tile one elected thread issues 3D bulk
 // tensor copies (cp.async.bulk.tensor) of the 9 f planes and the 9 h planes over the
 // tile plus a one-node ring (widened to XP columns each side for the 16-byte rule),
-// the 9 g planes and the 2 (phi u) planes over the tile, and for FP16 the 2 planes of
+// the 9 g planes and the 2 (phi u) planes over the tile, and for FP16 the 3 planes of
 // reference records over the tile plus a two-node ring, all completing on one mbarrier.  While a
 // tile is computed, the next tile's copies are in flight into the other stage.
 
@@ -385,7 +385,7 @@ struct TmaLayout {
     static constexpr int F_BYTES = 9 * FH * FW * (int)sizeof(E);
     static constexpr int G_BYTES = 9 * BY * BX * (int)sizeof(E);
     static constexpr int U_BYTES = 2 * BY * BX * 4;
-    static constexpr int R_BYTES = kRef<S> ? 2 * RH * RW * (int)sizeof(RefT) : 0;
+    static constexpr int R_BYTES = kRef<S> ? 3 * RH * RW * (int)sizeof(RefT) : 0;
     static constexpr int OFF_F = 0, OFF_H = rnd(F_BYTES), OFF_G = OFF_H + rnd(F_BYTES), OFF_U = OFF_G + rnd(G_BYTES),
                          OFF_R = OFF_U + rnd(U_BYTES), STAGE = OFF_R + rnd(R_BYTES);
     static constexpr uint32_t TX_BYTES = 2 * F_BYTES + G_BYTES + U_BYTES + R_BYTES;
@@ -395,7 +395,7 @@ struct TmaMaps {
     CUtensorMap popF;  // populations, box FW x FH x 9 (used for f at z = 0 and h at z = 18)
     CUtensorMap popG;  // populations, box BX x BY x 9 (g at z = 9)
     CUtensorMap phiu;  // (phi u) planes, box BX x BY x 2
-    CUtensorMap ref;   // FP16 reference records (8-byte elements), box RW x RH x 2
+    CUtensorMap ref;   // FP16 reference records (8-byte elements), box RW x RH x 3
 };
 
 // phi, T and 1/(rho c_p) of a TMA tile and its ring
@@ -407,13 +407,14 @@ struct PhiSmem {
     float irc[SN];
 };
 
-// CTAs per SM the TMA kernel is built for (shared memory allows 2 for FP32, 3 for
-// FP16; more CTAs means fewer registers per thread)
+// CTAs per SM the TMA kernel is built for (shared memory allows up to 2 for FP32 and
+// 3 for FP16; more CTAs means fewer registers per thread).  Measured on the 2048 x 512
+// channel: FP32 1 CTA 21.4 GLUPS vs 2 CTAs 20.8; FP16 2 CTAs 17.0 vs 3 CTAs 16.2.
 #ifndef TPF_TMA_BLOCKS_F32
-#define TPF_TMA_BLOCKS_F32 2
+#define TPF_TMA_BLOCKS_F32 1
 #endif
 #ifndef TPF_TMA_BLOCKS_F16
-#define TPF_TMA_BLOCKS_F16 3
+#define TPF_TMA_BLOCKS_F16 2
 #endif
 template <class S>
 constexpr int kTmaMinBlocks = kRef<S> ? TPF_TMA_BLOCKS_F16 : TPF_TMA_BLOCKS_F32;
@@ -489,7 +490,7 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         // decoded population i of ring slot (lx, ly) from the f (or h) box
         auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly) {
             float r = 0.f;
-            if constexpr (kRef<S>) r = ref_pop(i, ref_unpack(sR[(rplane * L::RH + ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i)]), false);
+            if constexpr (kRef<S>) r = ref_pop(i, ref_unpack(sR[(rplane * L::RH + ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i)]));
             return S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, r);
         };
 
@@ -506,11 +507,9 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
                 float rf = 0.f, rg = 0.f, rh = 0.f;
                 if constexpr (kRef<S>) {
                     const int k = (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i);
-                    const RefVals a = ref_unpack(sR[k]);
-                    const RefVals b = ref_unpack(sR[L::RH * L::RW + k]);
-                    rf = ref_pop(i, a, false);
-                    rg = wg(i) * a.w;
-                    rh = ref_pop(i, b, false);
+                    rf = ref_pop(i, ref_unpack(sR[kRecF * L::RH * L::RW + k]));
+                    rg = ref_g(i, ref_unpack(sR[kRecG * L::RH * L::RW + k]));
+                    rh = ref_pop(i, ref_unpack(sR[kRecH * L::RH * L::RW + k]));
                 }
                 f[i] = S::lds(sF, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_f, rf);
                 h[i] = S::lds(sH, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_h, rh);
@@ -534,12 +533,12 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
             float s = 0.f;
             if (tid < kRing) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, 0, i, rx, ry);
+                for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, kRecF, i, rx, ry);
                 sm.phi[k] = s;
                 sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(s), P.rcp_a));
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, 1, i, rx, ry);
+                for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, kRecH, i, rx, ry);
                 sm.T[k] = s;
             }
         }
@@ -553,11 +552,17 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
         phiu[n] = m.phi * m.ux;
         phiu[pl + n] = m.phi * m.uy;
+        RefVals rown_h{0.f, 0.f, 0.f};
+        if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
         collide_push<S, SX>(
             P, B, refB, x, y, kown, true, m, f, g, h,
-            [&](int i, int kd) { return decF(sH, P.is_h, 1, i, kd % SX, kd / SX); },
-            [&](int kd) { return sm.irc[kd]; }, [&](int kd) { return sm.phi[kd]; },
-            [&](int kd) { return sm.T[kd]; });
+            [&](int i, int kd) {
+                // h_i of destination kd came from this node: its reference is this node's record
+                float r = 0.f;
+                if constexpr (kRef<S>) r = ref_pop(i, rown_h);
+                return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
+            },
+            [&](int kd) { return sm.irc[kd]; });
         __syncthreads();  // stage s and sm are free for the copies issued next iteration
     }
 

@@ -74,8 +74,9 @@ __global__ void k_fields(const DevParams P, const typename S::elem* __restrict__
 }
 
 // Equilibrium populations from the staged fields (planes 0-4: phi, ux, uy, p, T).
-// FP16 records: (phi, 0, 0, p / cs2) and (T, 0, 0, 0) of each node, so that every
-// population is encoded against the rest equilibrium of its source (ref_source).
+// FP16 records: (phi, 0), (p / cs2, 0), (T, 0) of each node (first moments zero), so
+// that every population is encoded against the rest equilibrium of its writer
+// (ref_source).
 template <class S>
 __global__ void k_init(const DevParams P, const float* __restrict__ in, typename S::elem* __restrict__ A,
                        RefT* __restrict__ ref, float* __restrict__ phiu)
@@ -92,11 +93,10 @@ __global__ void k_init(const DevParams P, const float* __restrict__ in, typename
         for (int i = 0; i < 9; ++i) {
             float rf = 0.f, rg = 0.f, rh = 0.f;
             if constexpr (kRef<S>) {
-                bool self;
-                const int s = ref_source(P, x, y, i, self);
-                rf = wq(i) * half_round(in[s]);
-                rg = wg(i) * half_round(in[3 * pl + s] * kInvCs2);
-                rh = wq(i) * half_round(in[4 * pl + s]);
+                const int s = ref_source(P, x, y, i, false), sg = ref_source(P, x, y, i, true);
+                rf = wq(i) * in[s];
+                rg = wg(i) * (in[3 * pl + sg] * kInvCs2);
+                rh = wq(i) * in[4 * pl + s];
             }
             S::st(A + i * pl, n, f[i], P.s_f, rf);
             S::st(A + (9 + i) * pl, n, g[i], P.s_g, rg);
@@ -104,8 +104,9 @@ __global__ void k_init(const DevParams P, const float* __restrict__ in, typename
         }
         if constexpr (kRef<S>) {
             RefVals r;
-            ref[n] = ref_pack(phi, 0.f, 0.f, p * kInvCs2, r);
-            ref[pl + n] = ref_pack(T, 0.f, 0.f, 0.f, r);
+            ref[kRecF * pl + n] = ref_pack(phi, 0.f, 0.f, r);
+            ref[kRecG * pl + n] = ref_pack(p * kInvCs2, 0.f, 0.f, r);
+            ref[kRecH * pl + n] = ref_pack(T, 0.f, 0.f, r);
         }
         phiu[n] = phi * ux;
         phiu[pl + n] = phi * uy;
@@ -113,38 +114,30 @@ __global__ void k_init(const DevParams P, const float* __restrict__ in, typename
 }
 
 // State I/O of one LBE (k = 0 f, 1 g, 2 h) between 9 float32 staging planes and
-// storage.  For FP16, k_lbe_ref first sets the LBE's part of each node's record from
-// its staged populations: the zeroth moment (phi for f, T for h, first moments 0),
-// and for g the pressure estimate p / cs2 = sum_{i != 0} g_i / (1 - w_0) (Eq. 21
-// without its velocity terms; any value serves as long as encoder and decoder share
-// it).  The other LBEs' parts of the records are left as they are.
+// storage.  For FP16, k_lbe_ref first sets the LBE's record of each node from its
+// staged populations, first moments zero: the zeroth moment (phi for f, T for h), and
+// for g the pressure estimate p / cs2 = sum_{i != 0} g_i / (1 - w_0) (Eq. 21 without
+// its velocity terms; any value serves as long as encoder and decoder share it).
 __global__ void k_lbe_ref(const DevParams P, int k, const float* __restrict__ in, RefT* __restrict__ ref)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
-    __half* rh = reinterpret_cast<__half*>(ref);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         float r = 0.f;
 #pragma unroll
         for (int i = (k == 1 ? 1 : 0); i < 9; ++i) r += in[i * pl + n];
-        if (k == 1) {
-            rh[4 * n + 3] = __float2half_rn(r / (1.f - wq(0)));
-        } else {
-            __half* q = rh + 4 * ((k == 2 ? pl : 0) + n);
-            q[0] = __float2half_rn(r);
-            q[1] = __float2half_rn(0.f);
-            q[2] = __float2half_rn(0.f);
-        }
+        if (k == 1) r /= 1.f - wq(0);
+        RefVals v;
+        ref[k * pl + n] = ref_pack(r, 0.f, 0.f, v);
     }
 }
 // reference of population i of LBE k at (x, y)
 __device__ __forceinline__ float lbe_ref(const DevParams& P, int k, const RefT* __restrict__ ref, int x, int y, int i)
 {
-    bool self;
-    const int s = ref_source(P, x, y, i, self);
-    const RefVals r = ref_unpack(ref[(k == 2 ? P.plane : 0) + s]);
-    return k == 1 ? wg(i) * r.w : ref_pop(i, r, self);
+    const int s = ref_source(P, x, y, i, k == 1);
+    const RefVals r = ref_unpack(ref[k * P.plane + s]);
+    return k == 1 ? ref_g(i, r) : ref_pop(i, r);
 }
 template <class S>
 __global__ void k_lbe_encode(const DevParams P, int k, const float* __restrict__ in, typename S::elem* __restrict__ A,
@@ -224,13 +217,16 @@ k_reduce_partial(const DevParams P, const typename S::elem* __restrict__ A, cons
     }
 }
 
+// One warp per quantity: lane l adds blocks l, l + 32, ... in order, then a fixed
+// shuffle tree; the result does not depend on timing (deterministic).
 __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out)
 {
-    if (threadIdx.x < 8) {
-        double v = 0.0;
-        for (int b = 0; b < nblocks; ++b) v += partial[b * 8 + threadIdx.x];
-        out[threadIdx.x] = v;
-    }
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= 8) return;
+    double v = 0.0;
+    for (int b = lane; b < nblocks; b += 32) v += partial[b * 8 + k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[k] = v;
 }
 
 // Steady-state residual: FP64 sums of |u - u_snap|^2, |u|^2 and (T - T_snap)^2 per
@@ -370,8 +366,8 @@ Layout layout_of(int nx, int ny, int storage)
     size_t off = 0;
     L.pop0 = off; off = align256(off + 27 * (size_t)pl * e);
     L.pop1 = off; off = align256(off + 27 * (size_t)pl * e);
-    L.ref0 = off; off = align256(off + (f16 ? 2 * (size_t)pl * sizeof(RefT) : 0));
-    L.ref1 = off; off = align256(off + (f16 ? 2 * (size_t)pl * sizeof(RefT) : 0));
+    L.ref0 = off; off = align256(off + (f16 ? 3 * (size_t)pl * sizeof(RefT) : 0));
+    L.ref1 = off; off = align256(off + (f16 ? 3 * (size_t)pl * sizeof(RefT) : 0));
     L.phiu = off; off = align256(off + 2 * (size_t)pl * 4);
     L.stage = off; off = align256(off + kStagePlanes * (size_t)pl * 4);
     L.red = off; off = align256(off + (kRedMaxBlocks * 8 + 8) * sizeof(double));
@@ -525,7 +521,7 @@ void setup_tma(tpflbm_t h)
         bool ok = make_map(&M.popF, dt, e, h->pop[c], nx, ny, 27, pl, L::FW, L::FH, 9) &&
                   make_map(&M.popG, dt, e, h->pop[c], nx, ny, 27, pl, kBX, kBY, 9) &&
                   make_map(&M.phiu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->phiu, nx, ny, 2, pl, kBX, kBY, 2);
-        if (kRef<S>) ok = ok && make_map(&M.ref, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, h->ref[c], nx, ny, 2, pl, L::RW, L::RH, 2);
+        if (kRef<S>) ok = ok && make_map(&M.ref, CU_TENSOR_MAP_DATA_TYPE_UINT64, 8, h->ref[c], nx, ny, 3, pl, L::RW, L::RH, 3);
         else M.ref = M.phiu;
         if (!ok) return;
     }
@@ -839,7 +835,7 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8])
         k_reduce_partial<StoreF32><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const float*)h->pop[c], h->ref[c], h->phiu, h->red);
     TPF_CUDA(h, cudaGetLastError());
     double* res = h->red + kRedMaxBlocks * 8;
-    k_reduce_final<<<1, 32, 0, h->stream>>>(h->red, nb, res);
+    k_reduce_final<<<1, 256, 0, h->stream>>>(h->red, nb, res);
     TPF_CUDA(h, cudaGetLastError());
     TPF_CUDA(h, cudaMemcpyAsync(out, res, 8 * sizeof(double), cudaMemcpyDefault, h->stream));
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -892,7 +888,7 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("k_reduce_partial: ") + cudaGetErrorString(e));
     double* res = scratch + kRedMaxBlocks * 8;
-    k_reduce_final<<<1, 32, 0, s>>>(scratch, nb, res);
+    k_reduce_final<<<1, 256, 0, s>>>(scratch, nb, res);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 8 * sizeof(double), cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -918,7 +914,7 @@ int tpflbm_residual(tpflbm_t h, double dT, double out[3])
         k_residual_partial<StoreF32><<<nb, kRedThreads, 0, h->stream>>>(h->dp, (const float*)h->pop[c], h->ref[c], h->phiu, h->snap, h->red);
     TPF_CUDA(h, cudaGetLastError());
     double* res = h->red + kRedMaxBlocks * 8;
-    k_reduce_final<<<1, 32, 0, h->stream>>>(h->red, nb, res);
+    k_reduce_final<<<1, 256, 0, h->stream>>>(h->red, nb, res);
     TPF_CUDA(h, cudaGetLastError());
     double sums[8];
     TPF_CUDA(h, cudaMemcpyAsync(sums, res, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -964,7 +960,7 @@ int tpflbm_project_phi(tpflbm_t h, const float* phi_pred, double target_sum, int
     for (; it < 100; ++it) {
         k_project_partial<<<nb, kRedThreads, 0, h->stream>>>(a, N, s, h->red);
         TPF_CUDA(h, cudaGetLastError());
-        k_reduce_final<<<1, 32, 0, h->stream>>>(h->red, nb, res);
+        k_reduce_final<<<1, 256, 0, h->stream>>>(h->red, nb, res);
         TPF_CUDA(h, cudaGetLastError());
         TPF_CUDA(h, cudaMemcpyAsync(sums, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         TPF_CUDA(h, cudaStreamSynchronize(h->stream));
