@@ -114,6 +114,18 @@ int tpflbm_set_stream(tpflbm_t h, void *stream);
 int tpflbm_init(tpflbm_t h, const float *phi, const float *ux, const float *uy, const float *p,
                 const float *T);
 
+/* Same fields, with half of forcing sources taken off the equilibria: with bit 0 of
+ * `which`, f_i = f_i^eq - R_i / 2 (R_i: the interface term of the Allen-Cahn source,
+ * Eq. 14, with d_t(phi u) = 0); with bit 1, g_i = g_i^eq - G_i / 2 (G_i: the NS forcing
+ * of Sec. 3.1 with the interfacial force of Eq. 11 at the given phi, T and u).  The
+ * step adds its sources as (1 - 1/(2 tau)) S, so with which = 3 these populations
+ * decode to the given u and p exactly.  A lattice started near its steady state (a
+ * warm start) then skips part of the transient that equilibrium populations excite;
+ * which = 1, 2 or 3, anything else is TPF_ERR_INVALID_ARG.  The paper states no
+ * initialisation; tpflbm_init stays the plain equilibrium. */
+int tpflbm_init_forced(tpflbm_t h, const float *phi, const float *ux, const float *uy, const float *p,
+                       const float *T, int which);
+
 /* Advance nsteps >= 0 time steps (one fused step-kernel launch each), enqueued
  * on the handle's stream; returns after enqueueing. */
 int tpflbm_step(tpflbm_t h, long long nsteps);

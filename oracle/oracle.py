@@ -235,9 +235,12 @@ class OracleSim:
         return dict(zip(("phi", "ux", "uy", "p", "T"), out))
 
     def aux(self):
-        out = np.zeros((7, self.ny, self.nx))
+        """Per-node quantities of the macroscopic pass on the current state: density,
+        heat capacitance, thermal source, interfacial force, relaxation times, interface
+        normal and density gradient."""
+        out = np.zeros((11, self.ny, self.nx))
         self.lib.orc_get_aux(self.h, _dp(out))
-        return dict(zip(("rho", "rcp", "Fhat", "Fx", "Fy", "tau_g", "tau_h"), out))
+        return dict(zip(("rho", "rcp", "Fhat", "Fx", "Fy", "tau_g", "tau_h", "nx", "ny", "grx", "gry"), out))
 
     def get_state(self):
         f = np.zeros((9, self.ny, self.nx))

@@ -680,7 +680,8 @@ int orc_get_fields(orc_sim *s, double *phi, double *ux, double *uy, double *p, d
 }
 
 /* Extra per-node quantities of the current state for invariant checks:
- * out[k*N + n] for k = 0 rho, 1 rho c_p, 2 Fhat, 3 Fx, 4 Fy, 5 tau_g, 6 tau_h. */
+ * out[k*N + n] for k = 0 rho, 1 rho c_p, 2 Fhat, 3 Fx, 4 Fy, 5 tau_g, 6 tau_h,
+ * 7 n_x, 8 n_y (interface normal), 9, 10 grad rho. */
 int orc_get_aux(orc_sim *s, double *out)
 {
     macroscopic(s);
@@ -692,6 +693,10 @@ int orc_get_aux(orc_sim *s, double *out)
     to_double(out + 4 * N, s->Fy, N);
     to_double(out + 5 * N, s->tau_g, N);
     to_double(out + 6 * N, s->tau_h, N);
+    to_double(out + 7 * N, s->nx_, N);
+    to_double(out + 8 * N, s->ny_, N);
+    to_double(out + 9 * N, s->gradrx, N);
+    to_double(out + 10 * N, s->gradry, N);
     return 0;
 }
 

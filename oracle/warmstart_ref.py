@@ -73,3 +73,27 @@ def project_phi(phi, W, target_sum, mode="contour"):
     s = 0.5 * (lo + hi)
     out = np.tanh(a + s)
     return out, s, float(out.sum())
+
+
+def forced_init_state(nx, ny, params, fields):
+    """Populations of the half-source initialisation, from the FP64 oracle's own parts:
+    its equilibrium populations of the given fields, minus half of its Allen-Cahn
+    interface source R_i (d_t(phi u) = 0) and half of its NS forcing G_i, both with the
+    interface normal, density gradient and interfacial force of its macroscopic pass on
+    those fields (Eq. 11, Eq. 14, Sec. 3.1).  Returns the state dict of OracleSim."""
+    from .oracle import OracleSim, node_ops
+
+    o = OracleSim(nx, ny, params)
+    o.init(**{k: np.asarray(v, dtype=np.float64) for k, v in fields.items()})
+    st = o.get_state()
+    a = o.aux()
+    phi = np.asarray(fields["phi"], dtype=np.float64)
+    ux = np.asarray(fields["ux"], dtype=np.float64)
+    uy = np.asarray(fields["uy"], dtype=np.float64)
+    for y in range(ny):
+        for x in range(nx):
+            R = node_ops.Ri(phi[y, x], 0.0, 0.0, a["nx"][y, x], a["ny"][y, x], params["W"])
+            G = node_ops.Gi(ux[y, x], uy[y, x], a["grx"][y, x], a["gry"][y, x], a["Fx"][y, x], a["Fy"][y, x])
+            st["f"][:, y, x] -= 0.5 * R
+            st["g"][:, y, x] -= 0.5 * G
+    return st

@@ -77,9 +77,17 @@ __global__ void k_fields(const DevParams P, const typename S::elem* __restrict__
 // FP16 records: (phi, 0), (p / cs2, 0), (T, 0) of each node (first moments zero), so
 // that every population is encoded against the rest equilibrium of its writer
 // (ref_source).
-template <class S>
+//
+// With HALF_SRC, half of each selected forcing source is taken off the equilibria
+// (bit 0 of `which`: f_i -= R_i / 2 with R_i the interface term of the Allen-Cahn
+// source, d_t(phi u) = 0; bit 1: g_i -= G_i / 2 with the NS forcing at the given u).  For a scheme that adds its
+// source as (1 - 1/(2 tau)) S after the collision, these are the populations whose
+// moments decode to the given fields: sum_i c_i g_i + F/2 = rho u and the pressure
+// moment returns p.  The interfacial force, normal and density gradient come from
+// the same stencils and ghost values as in the step, evaluated on the given phi, T.
+template <class S, bool HALF_SRC>
 __global__ void k_init(const DevParams P, const float* __restrict__ in, typename S::elem* __restrict__ A,
-                       RefT* __restrict__ ref, float* __restrict__ phiu)
+                       RefT* __restrict__ ref, float* __restrict__ phiu, int which = 0)
 {
     const long long N = (long long)P.nx * P.ny;
     const long long pl = P.plane;
@@ -89,6 +97,26 @@ __global__ void k_init(const DevParams P, const float* __restrict__ in, typename
         const float phi = in[n], ux = in[pl + n], uy = in[2 * pl + n], p = in[3 * pl + n], T = in[4 * pl + n];
         float f[9], g[9], h[9];
         node_equilibria(P, phi, ux, uy, p, T, f, g, h);
+        if constexpr (HALF_SRC) {
+            auto get = [&](int gx, int gy, float& ph, float& tt) {
+                ph = in[(long long)gy * P.nx + gx];
+                tt = in[4 * pl + (long long)gy * P.nx + gx];
+            };
+            float phin[9], Tn[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) phiT_at(P, x + cx(i), y + cy(i), get, phin[i], Tn[i]);
+            const Macro m = node_macro(P, f, g, h, phin, Tn, phi * ux, phi * uy);
+            const float theta = (1.f - phi * phi) * P.theta_k;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const float cu = cx(i) * ux + cy(i) * uy;
+                const float Ri = wq(i) * theta * (cx(i) * m.nx + cy(i) * m.ny);
+                const float cg = cx(i) * m.grx + cy(i) * m.gry;
+                const float Gi = wq(i) * ((cx(i) * m.Fx + cy(i) * m.Fy) * kInvCs2 + cu * cg * kInvCs2);
+                if (which & 1) f[i] -= 0.5f * Ri;
+                if (which & 2) g[i] -= 0.5f * Gi;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             float rf = 0.f, rg = 0.f, rh = 0.f;
@@ -690,7 +718,8 @@ int tpflbm_set_stream(tpflbm_t h, void* stream)
     return TPF_OK;
 }
 
-int tpflbm_init(tpflbm_t h, const float* phi, const float* ux, const float* uy, const float* p, const float* T)
+static int init_impl(tpflbm_t h, const float* phi, const float* ux, const float* uy, const float* p, const float* T,
+                     int which)
 {
     if (!h) return TPF_ERR_INVALID_ARG;
     const float* src[5] = {phi, ux, uy, p, T};
@@ -700,16 +729,34 @@ int tpflbm_init(tpflbm_t h, const float* phi, const float* ux, const float* uy, 
     }
     const long long N = (long long)h->nx * h->ny;
     const int c = h->cur;
-    if (h->dp.storage == TPF_STORAGE_FP16)
-        k_init<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (__half*)h->pop[c], h->ref[c], h->phiu);
+    const bool f16 = h->dp.storage == TPF_STORAGE_FP16;
+    const bool half_src = which != 0;
+    if (f16 && half_src)
+        k_init<StoreF16, true><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (__half*)h->pop[c], h->ref[c], h->phiu, which);
+    else if (f16)
+        k_init<StoreF16, false><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (__half*)h->pop[c], h->ref[c], h->phiu);
+    else if (half_src)
+        k_init<StoreF32, true><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (float*)h->pop[c], h->ref[c], h->phiu, which);
     else
-        k_init<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (float*)h->pop[c], h->ref[c], h->phiu);
+        k_init<StoreF32, false><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, h->stage, (float*)h->pop[c], h->ref[c], h->phiu);
     TPF_CUDA(h, cudaGetLastError());
     // init reads the caller's buffers asynchronously: finish before returning
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     h->t = 0;
     h->snap_t = -1;
     return TPF_OK;
+}
+
+int tpflbm_init(tpflbm_t h, const float* phi, const float* ux, const float* uy, const float* p, const float* T)
+{
+    return init_impl(h, phi, ux, uy, p, T, 0);
+}
+
+int tpflbm_init_forced(tpflbm_t h, const float* phi, const float* ux, const float* uy, const float* p, const float* T,
+                       int which)
+{
+    if (which < 1 || which > 3) return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_init_forced: which must be 1, 2 or 3");
+    return init_impl(h, phi, ux, uy, p, T, which);
 }
 
 int tpflbm_step(tpflbm_t h, long long nsteps)

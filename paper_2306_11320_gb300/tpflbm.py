@@ -53,6 +53,7 @@ SIGNATURES = {
     "tpflbm_create_in": ([_ip, _ip, C.POINTER(Params), _vp, C.c_size_t, C.POINTER(_vp)], _ip),
     "tpflbm_set_stream": ([_vp, _vp], _ip),
     "tpflbm_init": ([_vp, _vp, _vp, _vp, _vp, _vp], _ip),
+    "tpflbm_init_forced": ([_vp, _vp, _vp, _vp, _vp, _vp, _ip], _ip),
     "tpflbm_step": ([_vp, C.c_longlong], _ip),
     "tpflbm_get_fields": ([_vp, _vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_get_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
@@ -189,9 +190,15 @@ class Lattice:
             pass
 
     # -------------------------------------------------------------------- API
-    def init(self, phi=None, ux=None, uy=None, p=None, T=None):
+    def init(self, phi=None, ux=None, uy=None, p=None, T=None, forced=0):
+        """Populations from fields: equilibria, or (forced = 1, 2, 3: bits for f, g)
+        equilibria less half of the forcing sources (tpflbm_init_forced; with 3 they
+        decode to exactly these u and p)."""
         arrs = [self._field(a) for a in (phi, ux, uy, p, T)]
-        self._check(self.lib.tpflbm_init(self.h, *[_ptr(a) for a in arrs]))
+        if forced:
+            self._check(self.lib.tpflbm_init_forced(self.h, *[_ptr(a) for a in arrs], int(forced)))
+        else:
+            self._check(self.lib.tpflbm_init(self.h, *[_ptr(a) for a in arrs]))
 
     def step(self, n: int = 1):
         self._check(self.lib.tpflbm_step(self.h, int(n)))

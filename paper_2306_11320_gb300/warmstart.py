@@ -16,8 +16,9 @@ Warm start (everything after the host-side parameter maps and cold-start fields 
 in the library's kernels): parameter maps -> bf16 NHWC input (tpfnet_pack) -> U-Net
 forward -> de-normalised planes plus the cold start (tpfnet_unpack) -> phi
 re-thresholded to the tanh profile about its predicted zero contour, shifted to the
-cold start's sum of phi (tpflbm_project_phi) -> equilibrium populations
-(tpflbm_init).
+cold start's sum of phi (tpflbm_project_phi) -> equilibrium populations (tpflbm_init;
+tpflbm_init_forced, which takes half of the forcing sources off, is an option that
+helped only from exact fields).
 """
 from __future__ import annotations
 
@@ -38,6 +39,7 @@ RESID_K = 1000                    # steps between residual evaluations
 OUT_FIELDS = ("phi", "ux", "uy", "p", "T")
 C_IN = 4
 CHANNELS = (32, 64, 128, 256)
+INIT_FORCED = 0                   # warm start populations: plain equilibria (measured best)
 
 
 # ------------------------------------------------------------------ instances
@@ -278,11 +280,12 @@ def predict(net, norm, insts):
     return planes
 
 
-def warm_init(lat, net, norm, inst):
-    """Initialise lattice `lat` from the network's prediction for `inst`."""
+def warm_init(lat, net, norm, inst, forced=INIT_FORCED):
+    """Initialise lattice `lat` from the network's prediction for `inst` (`forced`: the
+    half-source selection of tpflbm_init_forced, 0 for plain equilibria)."""
     planes = predict(net, norm, [inst])[0]
     phi, got = lat.project_phi(planes[0], cold_mass(inst), mode=1)
-    lat.init(phi=phi, ux=planes[1], uy=planes[2], p=planes[3], T=planes[4])
+    lat.init(phi=phi, ux=planes[1], uy=planes[2], p=planes[3], T=planes[4], forced=forced)
     return got
 
 
@@ -301,7 +304,7 @@ def time_to_steady(lat, tol, max_steps):
     return None, time.perf_counter() - t0
 
 
-def compare(net, norm, insts, tols=(1e-7, 1e-8), max_steps=800_000, log=print):
+def compare(net, norm, insts, tols=(1e-7, 1e-8), max_steps=800_000, log=print, forced=INIT_FORCED):
     """Cold versus warm start of each instance, on its own lattice and stream.
     Returns a list of dicts with steps and wall seconds to each tolerance."""
     import torch
@@ -322,7 +325,7 @@ def compare(net, norm, insts, tols=(1e-7, 1e-8), max_steps=800_000, log=print):
                     lat.init(**{n: v.astype(np.float32) for n, v in f.items()})
                 else:
                     net.stream = stream
-                    warm_init(lat, net, norm, inst)
+                    warm_init(lat, net, norm, inst, forced)
             torch.cuda.synchronize()
             t_init = time.perf_counter() - t0
             row[mode + "_init_s"] = t_init
@@ -406,6 +409,8 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="where to save the trained network (.npz)")
     ap.add_argument("--weights", default=None, help="skip generation and training: load this network")
     ap.add_argument("--json", default=None)
+    ap.add_argument("--init-forced", type=int, default=INIT_FORCED,
+                    help="warm start populations: 0 equilibria, 1/2/3 less half of the f/g/both sources")
     a = ap.parse_args(argv)
 
     def log(msg):
@@ -439,7 +444,8 @@ def main(argv=None):
         if a.out:
             save(a.out, net, norm, meta)
         del X, Y
-    res = compare(net, norm, test_i, max_steps=a.max_steps, log=log)
+    res = compare(net, norm, test_i, max_steps=a.max_steps, log=log, forced=a.init_forced)
+    summary["init_forced"] = a.init_forced
     summary.update(summarize(res, (1e-7, 1e-8)))
     if a.json:
         with open(a.json, "w") as fh:

@@ -148,6 +148,38 @@ def test_bubbles_full_size():
     _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
 
 
+@pytest.fixture(scope="module")
+def bubbles_1000():
+    """The 2048 x 512 two-bubble channel after 1000 steps in the FP64 and float32
+    oracles (about half a minute each on the host cores)."""
+    p, f, _ = WL.bubbles()
+    f32 = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in f.items()}
+    o = OracleSim(2048, 512, p)
+    o.init(**f32)
+    o.step(1000)
+    o32 = OracleSim(2048, 512, p, real="float")
+    o32.init(**f32)
+    o32.step(1000)
+    return p, f, o.fields(), o32.fields()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_bubbles_full_size_1000_steps(bubbles_1000, storage):
+    """The bench workload at its full size through the TMA kernel the bench times:
+    every field after 1000 steps within max(1e-5, 3 x the float32 floor) (FP32) or
+    5e-3 (FP16) of the FP64 oracle, compared on every node."""
+    p, f, ref, fl = bubbles_1000
+    if storage:
+        p = dict(p, **WL.fp16_scales(p))
+    lat = _lattice(2048, 512, p, storage=storage)
+    lat.init(**{k: np.asarray(v, dtype=np.float32) for k, v in f.items()})
+    lat.step(1000)
+    if storage:
+        _check_fields(lat.fields(), ref, 5e-3)
+    else:
+        _check_fields(lat.fields(), ref, 1e-5, fl)
+
+
 def test_mass_and_diagnostics():
     """FP64 device reductions against the oracle's fields; phi mass conserved in FP32."""
     nx, ny = 96, 64

@@ -39,6 +39,28 @@ def test_projection_matches_definition(mode, name, nx, ny):
     assert abs(out.cpu().numpy().astype(np.float64).sum() - target) <= 1e-6 * nx * ny
 
 
+@pytest.mark.parametrize("bc_x,bc_y", [(0, 0), (1, 0), (0, 1)])
+def test_forced_init_matches_reference(bc_x, bc_y):
+    """tpflbm_init_forced against the oracle-built populations (equilibria less half of
+    each forcing source), element by element, and the fields it decodes to equal the
+    fields it was given."""
+    from paper_2306_11320_gb300.tpflbm import Lattice
+
+    nx, ny = 96, 40
+    p, f, _ = WL.random_state(nx, ny, seed=4 + bc_x + 2 * bc_y, bc_x=bc_x, bc_y=bc_y)
+    f32 = {k: np.asarray(v, dtype=np.float32) for k, v in f.items()}
+    ref = R.forced_init_state(nx, ny, p, {k: v.astype(np.float64) for k, v in f32.items()})
+    lat = Lattice(nx, ny, p)
+    lat.init(**f32, forced=3)
+    st = lat.get_state()
+    for k in ("f", "g", "h"):
+        scale = np.abs(ref[k]).max()
+        assert np.abs(st[k] - ref[k]).max() <= 2e-6 * scale, k
+    got = lat.fields()
+    for k in ("phi", "ux", "uy", "p", "T"):
+        assert np.abs(got[k] - f32[k]).max() <= 1e-5 * max(1e-3, np.abs(f32[k]).max()), k
+
+
 def test_pack_unpack_with_base():
     from paper_2306_11320_gb300.unet import net_library
 
