@@ -469,15 +469,9 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         const int s = it & 1;
         const int tn = t + gridDim.x;
         if (tn < ntma && tid == 0) issue(tn, s ^ 1);
+        // every thread waits for the stage itself; a thread whose wait ran out reads
+        // stale (in-bounds) shared memory until the block votes at the next barrier
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(err, 1);
-                // let this CTA's other copy land (bounded) before leaving
-                if (tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
-            }
-            return;
-        }
         const unsigned char* st = dsm + s * L::STAGE;
         const E* sF = (const E*)(st + L::OFF_F);
         const E* sH = (const E*)(st + L::OFF_H);
@@ -542,7 +536,14 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
                 sm.T[k] = s;
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // let this CTA's other copy land (bounded) before leaving
+                if (tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int k = kown + cy(i) * SX + cx(i);
