@@ -72,6 +72,24 @@ def _traffic(storage):
     return None
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over all ranks (for times: the slowest rank's), or x
+    itself when running alone.  All ranks must call it."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes, steps, world, seconds):
+    """Whole-job rate in MLUPS: each of the `world` ranks advances its own replica of
+    `nodes` nodes by `steps` steps within `seconds` (the slowest rank's time)."""
+    return nodes * steps * world / seconds / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -207,11 +225,7 @@ def bench_ours(args, rank, world, local_rank):
                 flush.fill_(1)
             barrier()
         times = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), world, dev)
     diag = lat.diagnostics()
 
     # end to end through the public API with host buffers: H2D of the initial fields,
@@ -224,16 +238,12 @@ def bench_ours(args, rank, world, local_rank):
     lat.step(args.steps)
     lat._check(lat.lib.tpflbm_get_fields(lat.h, *[__import__("ctypes").c_void_p(t.data_ptr()) for t in host_out]))
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
 
     if rank != 0:
         return
     units = NX * NY * args.steps * world
-    value = units / (total_ms * 1e-3) / 1e6
+    value = job_mlups(NX * NY, args.steps, world, total_ms * 1e-3)
     per_launch_s = total_ms * 1e-3 / args.steps
     alg = ALG_BYTES[args.storage] * NX * NY
     peak, peak_kind = _peaks()
@@ -305,10 +315,7 @@ def bench_ensemble(args, rank, world, local_rank):
             e1.record(stream)
             torch.cuda.synchronize(dev)
         total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     d, rc = b.diagnostics()
     if rank != 0:
         return
@@ -317,7 +324,7 @@ def bench_ensemble(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     achieved = alg / (total_ms * 1e-3 / steps) / 1e9
     line = {
-        "metric": "coupled-LBM MLUPS", "value": nodes * steps * world / (total_ms * 1e-3) / 1e6, "unit": "MLUPS",
+        "metric": "coupled-LBM MLUPS", "value": job_mlups(nodes, steps, world, total_ms * 1e-3), "unit": "MLUPS",
         "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ensemble_256", "lattices": len(lats), "nodes": nodes, "storage": args.storage,
