@@ -62,6 +62,9 @@ typedef struct tpflbm *tpflbm_t;
  *   bc_y 0: halfway no-slip walls with Dirichlet temperature
  *       T_bottom(x) = T_bot + T_bot_amp cos(2 pi T_bot_k x / nx) + T_bot_slope x,
  *       T_top(x) = T_top + T_top_slope x (Sec. 4.1-4.3); 1: periodic in y.
+ *   normal_law: interface normal n in the Allen-Cahn source R_i (Eq. 14): 0 from the
+ *       isotropic stencil gradient of phi; 1 recovered locally from the populations
+ *       (Sec. 3): n = -J / |J| with J = sum_i c_i (f_i - f_i^eq) + d_t(phi u) / 2.
  *   storage: TPF_STORAGE_FP32 or TPF_STORAGE_FP16.  With FP16 a population q_i of
  *       LBE k is stored in float16 as s_k (q_i - r_i), its deviation from a
  *       reference that the node which wrote it (the node it streamed from; for a
@@ -84,7 +87,7 @@ typedef struct tpflbm_params {
     double u_ave, phi_in, T_in, p_out;
     double T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
     double fp16_scale_f, fp16_scale_g, fp16_scale_h;
-    int sigma_law, bc_x, bc_y, storage;
+    int sigma_law, bc_x, bc_y, storage, normal_law;
 } tpflbm_params;
 
 /* Device bytes tpflbm_create_in needs for an nx x ny lattice with these

@@ -28,7 +28,7 @@ _PARAM_DOUBLES = [
     "u_ave", "phi_in", "T_in", "p_out",
     "T_bot", "T_bot_amp", "T_bot_k", "T_bot_slope", "T_top", "T_top_slope",
 ]
-_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "pad_"]
+_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "normal_law"]
 
 
 class OrcParams(C.Structure):

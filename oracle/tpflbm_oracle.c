@@ -80,7 +80,7 @@ typedef struct {
     int sigma_law; /* 0 linear (Eq. 12), 1 parabolic (Eq. 63) */
     int bc_x;      /* 0 periodic, 1 velocity inlet at x=-1/2 and outflow at x=nx-1/2 */
     int bc_y;      /* 0 halfway no-slip walls at y=-1/2 and y=ny-1/2, 1 periodic */
-    int pad_;
+    int normal_law; /* interface normal in R_i: 0 from the stencil grad phi (R7), 1 local from f (Sec. 3) */
 } orc_params;
 
 /* the parameters in the oracle's arithmetic type */
@@ -91,7 +91,7 @@ typedef struct {
     real Gx, Gy;
     real u_ave, phi_in, T_in, p_out;
     real T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
-    int sigma_law, bc_x, bc_y;
+    int sigma_law, bc_x, bc_y, normal_law;
 } rparams;
 
 typedef struct {
@@ -326,6 +326,7 @@ static void real_params(const orc_params *P, rparams *R)
     R->sigma_law = P->sigma_law;
     R->bc_x = P->bc_x;
     R->bc_y = P->bc_y;
+    R->normal_law = P->normal_law;
 }
 
 static real *alloc0(size_t n) { return (real *)calloc(n, sizeof(real)); }
@@ -507,6 +508,27 @@ static void macroscopic(orc_sim *s)
             if (gn > 1e-10) {
                 nnx = gpx / gn;
                 nny = gpy / gn;
+            }
+            if (P->normal_law == 1) {
+                /* local recovery (Sec. 3): J = sum_i c_i (f_i - f_i^eq) + d_t(phi u) / 2
+                 * equals -cs2 tau_phi grad phi + M_phi Theta(phi) n with n the unit normal
+                 * (Theta = (1 - phi^2)/(sqrt2 W) for phi in [-1, 1]), and M_phi Theta <
+                 * cs2 tau_phi |grad phi| on the profile, so n = -J / |J| */
+                real feq[Q];
+                orc_feq(phi, ux, uy, feq);
+                real jx = 0.5 * dpx, jy = 0.5 * dpy;
+                for (int i = 0; i < Q; ++i) {
+                    real ne = s->f[i * N + n] - feq[i];
+                    jx += EX[i] * ne;
+                    jy += EY[i] * ne;
+                }
+                real jn = sqrt(jx * jx + jy * jy);
+                real tau_phi = P->M_phi / CS2 + 0.5;
+                nnx = nny = 0.0;
+                if (jn > 1e-10 * CS2 * tau_phi) {
+                    nnx = -jx / jn;
+                    nny = -jy / jn;
+                }
             }
 
             /* local temperature gradient from the non-equilibrium part of h (Eq. 40, R4) */

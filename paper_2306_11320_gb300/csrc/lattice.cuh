@@ -21,12 +21,13 @@ constexpr float kInvCs2 = 3.f;
 
 // Everything a kernel needs, precomputed on the host from tpflbm_params.
 struct DevParams {
-    int nx, ny, bc_x, bc_y, sigma_law, storage;
+    int nx, ny, bc_x, bc_y, sigma_law, storage, normal_law;
     long long plane;  // elements per population plane (>= nx*ny, padded)
     // Eq. 45 as a + b * clamp(phi): value = (xi_l + xi_h)/2 + (xi_h - xi_l)/2 * phi
     float rho_a, rho_b, mu_a, mu_b, lam_a, lam_b, rcp_a, rcp_b;
     float drho_dphi;  // (rho_h - rho_l)/2, derivative of Eq. 8
     float W2, inv_W2, theta_k;  // W^2, 1/W^2, 1/(sqrt2 W)
+    float jthr2;      // local normal: |J|^2 below which n = 0 ((1e-10 cs2 tau_phi)^2)
     float kFs;                  // 3 sqrt2 W / 4 (Eq. 11)
     float inv_tau_phi, src_phi; // 1/tau_phi, 1 - 1/(2 tau_phi)
     float sigma_ref, sigma_T, sigma_TT, T_ref;
@@ -174,11 +175,25 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     m.dpuy = phi * uy - puy_prev;
 
     // unit normal; zero where |grad phi| <= 1e-10
-    const float gn2 = g2;
-    if (gn2 > 1e-20f) {
+    float nvx = gpx, nvy = gpy, nthr = 1e-20f;
+    if (P.normal_law == 1) {
+        // local recovery (Sec. 3): J = sum_i c_i (f_i - f_i^eq) + d_t(phi u)/2 =
+        // -cs2 tau_phi grad phi + M_phi Theta n, so n = -J/|J|; sum_i c_i f_i^eq = phi u
+        float jx = 0.5f * m.dpux - phi * ux, jy = 0.5f * m.dpuy - phi * uy;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (cx(i) != 0) jx += (float)cx(i) * f[i];
+            if (cy(i) != 0) jy += (float)cy(i) * f[i];
+        }
+        nvx = -jx;
+        nvy = -jy;
+        nthr = P.jthr2;
+    }
+    const float gn2 = nvx * nvx + nvy * nvy;
+    if (gn2 > nthr) {
         const float r = rsqrtf(gn2);
-        m.nx = gpx * r;
-        m.ny = gpy * r;
+        m.nx = nvx * r;
+        m.ny = nvy * r;
     } else {
         m.nx = 0.f;
         m.ny = 0.f;
@@ -193,7 +208,6 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     }
     const float k = -m.inv_tau_h * kInvCs2;
     m.Fhat = -rcp * (ux * qx + uy * qy) * k;
-    (void)f;
     return m;
 }
 

@@ -442,6 +442,7 @@ int validate(int nx, int ny, const tpflbm_params* p, std::string& why)
     if (p->storage != TPF_STORAGE_FP32 && p->storage != TPF_STORAGE_FP16) { why = "unknown storage"; return TPF_ERR_INVALID_ARG; }
     if (p->bc_x < 0 || p->bc_x > 1 || p->bc_y < 0 || p->bc_y > 1) { why = "bc_x/bc_y must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
     if (p->sigma_law < 0 || p->sigma_law > 1) { why = "sigma_law must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
+    if (p->normal_law < 0 || p->normal_law > 1) { why = "normal_law must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
     if (!(p->rho_l > 0 && p->rho_h > 0)) { why = "densities must be positive"; return TPF_ERR_INVALID_ARG; }
     if (!(p->mu_l > 0 && p->mu_h > 0 && p->lambda_l > 0 && p->lambda_h > 0)) { why = "mu and lambda must be positive (tau > 1/2)"; return TPF_ERR_INVALID_ARG; }
     if (!(p->cp_l > 0 && p->cp_h > 0)) { why = "heat capacities must be positive"; return TPF_ERR_INVALID_ARG; }
@@ -461,6 +462,7 @@ DevParams make_dev_params(int nx, int ny, const tpflbm_params& p)
 {
     DevParams d{};
     d.nx = nx; d.ny = ny; d.bc_x = p.bc_x; d.bc_y = p.bc_y; d.sigma_law = p.sigma_law; d.storage = p.storage;
+    d.normal_law = p.normal_law;
     d.plane = plane_of(nx, ny);
     auto ab = [](double l, double h, float& a, float& b) { a = (float)(0.5 * (l + h)); b = (float)(0.5 * (h - l)); };
     ab(p.rho_l, p.rho_h, d.rho_a, d.rho_b);
@@ -474,6 +476,7 @@ DevParams make_dev_params(int nx, int ny, const tpflbm_params& p)
     d.kFs = (float)(3.0 * std::sqrt(2.0) * p.W / 4.0);
     const double tau_phi = p.M_phi * 3.0 + 0.5;
     d.inv_tau_phi = (float)(1.0 / tau_phi);
+    d.jthr2 = (float)((1e-10 / 3.0 * tau_phi) * (1e-10 / 3.0 * tau_phi));
     d.src_phi = (float)(1.0 - 0.5 / tau_phi);
     d.sigma_ref = (float)p.sigma_ref; d.sigma_T = (float)p.sigma_T; d.sigma_TT = (float)p.sigma_TT; d.T_ref = (float)p.T_ref;
     d.Gx = (float)p.Gx; d.Gy = (float)p.Gy;

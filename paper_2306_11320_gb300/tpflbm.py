@@ -24,7 +24,7 @@ _PARAM_DOUBLES = [
     "T_bot", "T_bot_amp", "T_bot_k", "T_bot_slope", "T_top", "T_top_slope",
     "fp16_scale_f", "fp16_scale_g", "fp16_scale_h",
 ]
-_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "storage"]
+_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "storage", "normal_law"]
 
 STORAGE_FP32 = 0
 STORAGE_FP16 = 1

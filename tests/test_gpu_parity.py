@@ -180,6 +180,23 @@ def test_bubbles_full_size_1000_steps(bubbles_1000, storage):
         _check_fields(lat.fields(), ref, 1e-5, fl)
 
 
+@pytest.mark.parametrize("case", ["random", "drop"])
+def test_local_normal_law(case):
+    """The local interface normal (normal_law = 1) against the oracle with the same law."""
+    if case == "random":
+        nx, ny = 96, 48
+        p, f, _ = WL.random_state(nx, ny, seed=8, bc_x=0, bc_y=0, sigma_law=0)
+        steps = 200
+    else:
+        nx, ny = 256, 1024
+        p, f, _ = WL.drop_migration(Ma=10.0)
+        steps = 300
+    p = dict(p, normal_law=1)
+    gpu, orc, o32 = _pair(nx, ny, p, f, floor=True)
+    _run_all((gpu, orc, o32), steps)
+    _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
+
+
 def test_mass_and_diagnostics():
     """FP64 device reductions against the oracle's fields; phi mass conserved in FP32."""
     nx, ny = 96, 64
