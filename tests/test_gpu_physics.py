@@ -61,3 +61,39 @@ def test_marangoni_number_trend():
         out[Ma] = d["Ur_num"] / d["Ur_den"] / m["U_ygb"]
     print("U_r / U_YGB:", out)
     assert out[10.0] < out[0.1]
+
+
+def test_finite_marangoni_sweep_at_re_1():
+    """Sec. 4.2 at finite Marangoni number: Re = 1, Ma = 1, 10, 100 set through c_p with
+    the conductivity fixed, equal property ratios.  The paper reports that (i) early on
+    the drop speeds up alike for every Ma, (ii) Ma = 1 settles without overshoot while
+    Ma >= 10 first overshoots and then slows to its terminal speed, and (iii) the
+    terminal speed decreases with Ma.  Terminal: the mean over t U/R in [30, 46], where
+    every case has settled (the Ma = 100 temperature field needs about 30 R/U); later
+    the drop feels the hot wall of this 1024-high channel (beyond about 60 R/U)."""
+    hist = {}
+    for Ma in (1.0, 10.0, 100.0):
+        p, f, m = WL.drop_migration(Ma=Ma, Re=1.0, ratio=1.0)
+        lat = _lat(256, 1024, p, f)
+        us = []
+        for _ in range(92):
+            lat.step(2560)
+            d = lat.diagnostics()
+            assert d["nonfinite"] == 0
+            us.append(d["Ur_num"] / d["Ur_den"] / m["U_ygb"])
+        hist[Ma] = np.array(us)
+    t = 2560 * np.arange(1, 93) / (m["R"] / m["U"])      # R / U = 5120 steps at Re = 1
+    win = (t >= 30) & (t <= 46)
+    term = {Ma: u[win].mean() for Ma, u in hist.items()}
+    for Ma, u in hist.items():
+        print("Ma %g: U_r/U_YGB at t U/R = 0.5, 1, 2, 4, 8, 16, 32:" % Ma,
+              ["%.3f" % u[np.argmin(np.abs(t - s))] for s in (0.5, 1, 2, 4, 8, 16, 32)],
+              "peak %.3f at %.1f, terminal %.3f" % (u.max(), t[u.argmax()], term[Ma]))
+        assert np.ptp(u[win]) < 0.04 * term[Ma], (Ma, np.ptp(u[win]) / term[Ma])  # settled
+    for s in (0.5, 1.0):
+        early = [u[np.argmin(np.abs(t - s))] for u in hist.values()]
+        assert np.ptp(early) < 0.02 * max(early)                              # (i)
+    assert hist[1.0].max() < 1.01 * term[1.0]                                # (ii) Ma = 1 settles from below
+    for Ma in (10.0, 100.0):
+        assert hist[Ma].max() > 1.03 * term[Ma], (Ma, hist[Ma].max(), term[Ma])  # (ii) overshoot
+    assert term[1.0] > term[10.0] > term[100.0] > 0                          # (iii)
