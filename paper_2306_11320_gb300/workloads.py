@@ -130,6 +130,35 @@ def drop_migration(nx=256, ny=1024, R=32.0, Ma=0.1, Re=0.1, Ca=0.08, ratio=0.5,
     return params, fields, meta
 
 
+def drop_density_ratio(rho_r, nx=160, ny=320, R=20.0, W=DEFAULT_W, M_phi=DEFAULT_M_PHI, T_c=16.0):
+    """The high-density-ratio drop of Table 2 (Sec. 4.2), on the paper's 160 x 320 lattice
+    (periodic in x, walls in y) with R = 20.
+
+    Printed: sigma_ref = 2.5e-4, sigma_T = -1e-5, mu = 0.8, (rho c_p)_h = 5,
+    (rho c_p)_l = 1, Re = 0.00625, Ma = 0.0125, Ca = 0.08.  The printed U_YGB column
+    follows with U = 2.5e-5, lambda_r = 0.5 and mu_r = 1 / rho_r (the paper's "mu_l =
+    mu_h" does not reproduce it); U = -sigma_T grad T R / mu_h then needs grad T = 0.1,
+    Re = rho_h U R / mu_h needs rho_h = 10, so the drop has rho_l = 10 / rho_r and the
+    same kinematic viscosity, and Ma = U R (rho c_p)_h / lambda_h gives lambda_h = 0.2.
+    """
+    mu_h, rho_h, sigma_T, sigma_ref, gradT = 0.8, 10.0, -1e-5, 2.5e-4, 0.1
+    U = -sigma_T * gradT * R / mu_h
+    lambda_h = U * R * 5.0 / 0.0125
+    xc, yc = 0.5 * (nx - 1), 0.5 * (ny - 1)
+    params = base_params(
+        rho_l=rho_h / rho_r, rho_h=rho_h, mu_l=mu_h / rho_r, mu_h=mu_h,
+        lambda_l=0.5 * lambda_h, lambda_h=lambda_h, cp_l=rho_r / rho_h, cp_h=5.0 / rho_h,
+        W=W, M_phi=M_phi, sigma_law=0, sigma_ref=sigma_ref, sigma_T=sigma_T,
+        T_ref=T_c + gradT * (yc + 0.5), bc_x=0, bc_y=0, T_bot=T_c, T_top=T_c + gradT * ny,
+    )
+    x, y = _grid(nx, ny)
+    phi = _profile(np.hypot(x - xc, y - yc) - R, W)
+    z = np.zeros_like(phi)
+    fields = dict(phi=phi, ux=z.copy(), uy=z.copy(), p=z.copy(), T=T_c + gradT * (y + 0.5))
+    U_ygb = young_speed(U, 1.0 / rho_r, 0.5)
+    return params, fields, dict(name="drop_rho", R=R, U=U, U_ygb=U_ygb, rho_r=rho_r)
+
+
 def young_speed(U, mu_r, lam_r):
     """Young-Goldstein-Block terminal speed, Eq. 60."""
     return 2.0 * U / ((2.0 + 3.0 * mu_r) * (2.0 + lam_r))
