@@ -200,6 +200,8 @@ def bench_ours(args, rank, world, local_rank):
     if storage == STORAGE_FP16:
         params.update(WL.fp16_scales(params))
     params["normal_law"] = 1 if args.normal == "local" else 0
+    if args.collision == "trt":
+        params.update(collision=1, trt_lambda=0.25)
     stream = torch.cuda.Stream(device=dev)
     lat = Lattice(NX, NY, params, storage=storage, stream=stream)
     f32 = {k: v.astype(np.float32) for k, v in fields.items()}
@@ -260,7 +262,7 @@ def bench_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "storage": args.storage, "normal": args.normal,
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "storage": args.storage, "normal": args.normal, "collision": args.collision,
                    "l2": "256 MiB L2 flush between timed steps", "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(args.storage),
@@ -389,6 +391,8 @@ def main():
                          "256-lattice parameter sweep through the batched launch; warmstart: time to "
                          "steady state, cold vs learned warm start, on held-out microchannels")
     ap.add_argument("--instances", type=int, default=8, help="warmstart: held-out instances to time")
+    ap.add_argument("--collision", choices=("bgk", "trt"), default="bgk",
+                    help="NS and thermal collision operator: BGK (the paper's) or two relaxation times")
     ap.add_argument("--normal", choices=("stencil", "local"), default="stencil",
                     help="interface normal of the Allen-Cahn source: stencil gradient or local recovery")
     args = ap.parse_args()

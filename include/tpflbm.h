@@ -62,6 +62,13 @@ typedef struct tpflbm *tpflbm_t;
  *   bc_y 0: halfway no-slip walls with Dirichlet temperature
  *       T_bottom(x) = T_bot + T_bot_amp cos(2 pi T_bot_k x / nx) + T_bot_slope x,
  *       T_top(x) = T_top + T_top_slope x (Sec. 4.1-4.3); 1: periodic in y.
+ *   collision: 0 BGK for every LBE (Sec. 3); 1 two relaxation times for the NS and
+ *       thermal LBEs (the stability extension the paper points to in Sec. 3): with
+ *       X^{+/-} = (X_i +/- X_opp(i))/2 the even and odd parts relax at 1/tau+ and
+ *       1/tau-, (tau+ - 1/2)(tau- - 1/2) = trt_lambda (> 0), tau+ = tau_g for g
+ *       (viscosity), tau- = tau_h for h (conductivity); the NS source splits with
+ *       factors 1 - 1/(2 tau+/-).  trt_lambda = 3/16 makes halfway bounce-back walls
+ *       exact for Poiseuille flow; (tau - 1/2)^2 gives BGK back.
  *   normal_law: interface normal n in the Allen-Cahn source R_i (Eq. 14): 0 from the
  *       isotropic stencil gradient of phi; 1 recovered locally from the populations
  *       (Sec. 3): n = -J / |J| with J = sum_i c_i (f_i - f_i^eq) + d_t(phi u) / 2.
@@ -87,7 +94,8 @@ typedef struct tpflbm_params {
     double u_ave, phi_in, T_in, p_out;
     double T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
     double fp16_scale_f, fp16_scale_g, fp16_scale_h;
-    int sigma_law, bc_x, bc_y, storage, normal_law;
+    double trt_lambda;
+    int sigma_law, bc_x, bc_y, storage, normal_law, collision;
 } tpflbm_params;
 
 /* Device bytes tpflbm_create_in needs for an nx x ny lattice with these

@@ -27,8 +27,9 @@ _PARAM_DOUBLES = [
     "Gx", "Gy",
     "u_ave", "phi_in", "T_in", "p_out",
     "T_bot", "T_bot_amp", "T_bot_k", "T_bot_slope", "T_top", "T_top_slope",
+    "trt_lambda",
 ]
-_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "normal_law"]
+_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "normal_law", "collision"]
 
 
 class OrcParams(C.Structure):

@@ -77,10 +77,12 @@ typedef struct {
     double Gx, Gy;
     double u_ave, phi_in, T_in, p_out;
     double T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
+    double trt_lambda; /* two-relaxation-time "magic" parameter (tau+ - 1/2)(tau- - 1/2) */
     int sigma_law; /* 0 linear (Eq. 12), 1 parabolic (Eq. 63) */
     int bc_x;      /* 0 periodic, 1 velocity inlet at x=-1/2 and outflow at x=nx-1/2 */
     int bc_y;      /* 0 halfway no-slip walls at y=-1/2 and y=ny-1/2, 1 periodic */
     int normal_law; /* interface normal in R_i: 0 from the stencil grad phi (R7), 1 local from f (Sec. 3) */
+    int collision;  /* g and h LBEs: 0 BGK (Sec. 3), 1 two relaxation times (TRT) */
 } orc_params;
 
 /* the parameters in the oracle's arithmetic type */
@@ -91,7 +93,8 @@ typedef struct {
     real Gx, Gy;
     real u_ave, phi_in, T_in, p_out;
     real T_bot, T_bot_amp, T_bot_k, T_bot_slope, T_top, T_top_slope;
-    int sigma_law, bc_x, bc_y, normal_law;
+    real trt_lambda;
+    int sigma_law, bc_x, bc_y, normal_law, collision;
 } rparams;
 
 typedef struct {
@@ -327,6 +330,8 @@ static void real_params(const orc_params *P, rparams *R)
     R->bc_x = P->bc_x;
     R->bc_y = P->bc_y;
     R->normal_law = P->normal_law;
+    R->collision = P->collision;
+    R->trt_lambda = (real)P->trt_lambda;
 }
 
 static real *alloc0(size_t n) { return (real *)calloc(n, sizeof(real)); }
@@ -551,6 +556,26 @@ static void macroscopic(orc_sim *s)
 
 /* ------------------------------------------------------- pass 3: collide */
 
+/* Two-relaxation-time collision of population i (the extension the paper points to
+ * for stability, Sec. 3): with X_i^{+/-} = (X_i +/- X_opp(i)) / 2 for the populations q,
+ * their equilibria e and the source S,
+ *   q*_i = q_i - (q_i^+ - e_i^+) / tau_p - (q_i^- - e_i^-) / tau_m + c^+ S_i^+ + c^- S_i^-,
+ * c^{+/-} = 1 - 1/(2 tau_{+/-}) when the source carries the half-step factor (NS LBE),
+ * 1 otherwise (thermal LBE).  tau_p = tau_m is the BGK collision. */
+static real trt_one(const real *q, size_t N, size_t n, int i, const real *e, const real *src,
+                    real tau_p, real tau_m, int half_step_source)
+{
+    int o = 0;
+    for (int j = 0; j < Q; ++j)
+        if (EX[j] == -EX[i] && EY[j] == -EY[i]) o = j;
+    real qp = 0.5 * (q[i * N + n] + q[o * N + n]), qm = 0.5 * (q[i * N + n] - q[o * N + n]);
+    real ep = 0.5 * (e[i] + e[o]), em = 0.5 * (e[i] - e[o]);
+    real sp = 0.5 * (src[i] + src[o]), sm = 0.5 * (src[i] - src[o]);
+    real cp = half_step_source ? 1.0 - 0.5 / tau_p : 1.0;
+    real cm = half_step_source ? 1.0 - 0.5 / tau_m : 1.0;
+    return q[i * N + n] - (qp - ep) / tau_p - (qm - em) / tau_m + cp * sp + cm * sm;
+}
+
 static void collide(orc_sim *s)
 {
     const rparams *P = &s->R;
@@ -576,9 +601,16 @@ static void collide(orc_sim *s)
             real tg = s->tau_g[n];
             orc_geq(s->p[n], s->rho[n], s->ux[n], s->uy[n], eq);
             orc_Gi(s->ux[n], s->uy[n], s->gradrx[n], s->gradry[n], s->Fx[n], s->Fy[n], src);
-            for (int i = 0; i < Q; ++i) {
-                real gi = s->g[i * N + n];
-                s->gs[i * N + n] = gi - (gi - eq[i]) / tg + (1.0 - 0.5 / tg) * src[i];
+            if (P->collision == 1) {
+                /* TRT: the viscosity stays on the even part (tau+ = tau_g) */
+                real tm = 0.5 + P->trt_lambda / (tg - 0.5);
+                for (int i = 0; i < Q; ++i)
+                    s->gs[i * N + n] = trt_one(s->g, N, n, i, eq, src, tg, tm, 1);
+            } else {
+                for (int i = 0; i < Q; ++i) {
+                    real gi = s->g[i * N + n];
+                    s->gs[i * N + n] = gi - (gi - eq[i]) / tg + (1.0 - 0.5 / tg) * src[i];
+                }
             }
 
             /* thermal LBE, Eq. 28: collision part (the rho c_p weighting is applied
@@ -586,9 +618,16 @@ static void collide(orc_sim *s)
             real th = s->tau_h[n];
             orc_heq(s->T[n], eq);
             orc_Fhat_i(s->Fhat[n], src);
-            for (int i = 0; i < Q; ++i) {
-                real hi = s->h[i * N + n];
-                s->hs[i * N + n] = hi - (hi - eq[i]) / th + src[i];
+            if (P->collision == 1) {
+                /* TRT: the conductivity stays on the odd part (tau- = tau_h) */
+                real tp = 0.5 + P->trt_lambda / (th - 0.5);
+                for (int i = 0; i < Q; ++i)
+                    s->hs[i * N + n] = trt_one(s->h, N, n, i, eq, src, tp, th, 0);
+            } else {
+                for (int i = 0; i < Q; ++i) {
+                    real hi = s->h[i * N + n];
+                    s->hs[i * N + n] = hi - (hi - eq[i]) / th + src[i];
+                }
             }
         }
 }

@@ -21,13 +21,14 @@ constexpr float kInvCs2 = 3.f;
 
 // Everything a kernel needs, precomputed on the host from tpflbm_params.
 struct DevParams {
-    int nx, ny, bc_x, bc_y, sigma_law, storage, normal_law;
+    int nx, ny, bc_x, bc_y, sigma_law, storage, normal_law, collision;
     long long plane;  // elements per population plane (>= nx*ny, padded)
     // Eq. 45 as a + b * clamp(phi): value = (xi_l + xi_h)/2 + (xi_h - xi_l)/2 * phi
     float rho_a, rho_b, mu_a, mu_b, lam_a, lam_b, rcp_a, rcp_b;
     float drho_dphi;  // (rho_h - rho_l)/2, derivative of Eq. 8
     float W2, inv_W2, theta_k;  // W^2, 1/W^2, 1/(sqrt2 W)
     float jthr2;      // local normal: |J|^2 below which n = 0 ((1e-10 cs2 tau_phi)^2)
+    float trt_lambda; // TRT magic parameter (collision == 1)
     float kFs;                  // 3 sqrt2 W / 4 (Eq. 11)
     float inv_tau_phi, src_phi; // 1/tau_phi, 1 - 1/(2 tau_phi)
     float sigma_ref, sigma_T, sigma_TT, T_ref;
@@ -250,19 +251,53 @@ __device__ __forceinline__ void node_collide(const DevParams& P, const Macro& m,
     const float Fh = m.Fhat;
     float feq[9], geq[9], heq[9];
     node_equilibria_(m.phi, m.rho, ux, uy, m.p, m.T, feq, geq, heq);
+    float Gs[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float cu = cx(i) * ux + cy(i) * uy;
         // Allen-Cahn with source R_i
         const float Ri = wq(i) * (cx(i) * ax + cy(i) * ay);
         f[i] = f[i] + (feq[i] - f[i]) * P.inv_tau_phi + P.src_phi * Ri;
-        // Navier-Stokes with forcing G_i; its u.grad rho terms cancel:
+        // Navier-Stokes forcing; its u.grad rho terms cancel:
         // G_i = w_i [ c_i.(Fs + G)/cs2 + (c_i.u)(c_i.grad rho)/cs2 ]
         const float cg = cx(i) * m.grx + cy(i) * m.gry;
-        const float Gi = wq(i) * (cx(i) * FxC + cy(i) * FyC + cu * cg * kInvCs2);
-        g[i] = g[i] + (geq[i] - g[i]) * m.inv_tau_g + m.src_g * Gi;
-        // thermal with source w_i Fhat
-        h[i] = h[i] + (heq[i] - h[i]) * m.inv_tau_h + wq(i) * Fh;
+        Gs[i] = wq(i) * (cx(i) * FxC + cy(i) * FyC + cu * cg * kInvCs2);
+    }
+    if (P.collision == 1) {
+        // two relaxation times (the stability extension of Sec. 3) for g and h: with
+        // X^{+/-} = (X_i +/- X_opp(i)) / 2, the even part relaxes at om_p, the odd part at
+        // om_m, (tau_p - 1/2)(tau_m - 1/2) = Lambda; the viscosity stays on the even part
+        // of g (tau_p = tau_g), the conductivity on the odd part of h (tau_m = tau_h)
+        const float og_p = m.inv_tau_g;
+        const float og_m = __frcp_rn(0.5f + P.trt_lambda * __frcp_rn(__frcp_rn(og_p) - 0.5f));
+        const float oh_m = m.inv_tau_h;
+        const float oh_p = __frcp_rn(0.5f + P.trt_lambda * __frcp_rn(__frcp_rn(oh_m) - 0.5f));
+        const float cg_p = 1.f - 0.5f * og_p, cg_m = 1.f - 0.5f * og_m;
+        g[0] = g[0] + (geq[0] - g[0]) * og_p + cg_p * Gs[0];
+        h[0] = h[0] + (heq[0] - h[0]) * oh_p + wq(0) * Fh;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int o = opp(i);
+            if (o < i) continue;  // each pair once
+            const float gp = 0.5f * (g[i] + g[o]), gm = 0.5f * (g[i] - g[o]);
+            const float ep = 0.5f * (geq[i] + geq[o]), em = 0.5f * (geq[i] - geq[o]);
+            const float sp = 0.5f * (Gs[i] + Gs[o]), sm = 0.5f * (Gs[i] - Gs[o]);
+            const float dp = (ep - gp) * og_p + cg_p * sp, dm = (em - gm) * og_m + cg_m * sm;
+            g[i] = g[i] + dp + dm;
+            g[o] = g[o] + dp - dm;
+            const float hp = 0.5f * (h[i] + h[o]), hm = 0.5f * (h[i] - h[o]);
+            const float hep = 0.5f * (heq[i] + heq[o]), hem = 0.5f * (heq[i] - heq[o]);
+            const float hdp = (hep - hp) * oh_p + wq(i) * Fh, hdm = (hem - hm) * oh_m;
+            h[i] = h[i] + hdp + hdm;
+            h[o] = h[o] + hdp - hdm;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            g[i] = g[i] + (geq[i] - g[i]) * m.inv_tau_g + m.src_g * Gs[i];
+            // thermal with source w_i Fhat
+            h[i] = h[i] + (heq[i] - h[i]) * m.inv_tau_h + wq(i) * Fh;
+        }
     }
 }
 

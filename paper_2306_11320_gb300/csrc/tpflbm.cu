@@ -443,6 +443,8 @@ int validate(int nx, int ny, const tpflbm_params* p, std::string& why)
     if (p->bc_x < 0 || p->bc_x > 1 || p->bc_y < 0 || p->bc_y > 1) { why = "bc_x/bc_y must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
     if (p->sigma_law < 0 || p->sigma_law > 1) { why = "sigma_law must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
     if (p->normal_law < 0 || p->normal_law > 1) { why = "normal_law must be 0 or 1"; return TPF_ERR_INVALID_ARG; }
+    if (p->collision < 0 || p->collision > 1) { why = "collision must be 0 (BGK) or 1 (TRT)"; return TPF_ERR_INVALID_ARG; }
+    if (p->collision == 1 && !(p->trt_lambda > 0.0)) { why = "TRT needs trt_lambda > 0"; return TPF_ERR_INVALID_ARG; }
     if (!(p->rho_l > 0 && p->rho_h > 0)) { why = "densities must be positive"; return TPF_ERR_INVALID_ARG; }
     if (!(p->mu_l > 0 && p->mu_h > 0 && p->lambda_l > 0 && p->lambda_h > 0)) { why = "mu and lambda must be positive (tau > 1/2)"; return TPF_ERR_INVALID_ARG; }
     if (!(p->cp_l > 0 && p->cp_h > 0)) { why = "heat capacities must be positive"; return TPF_ERR_INVALID_ARG; }
@@ -463,6 +465,8 @@ DevParams make_dev_params(int nx, int ny, const tpflbm_params& p)
     DevParams d{};
     d.nx = nx; d.ny = ny; d.bc_x = p.bc_x; d.bc_y = p.bc_y; d.sigma_law = p.sigma_law; d.storage = p.storage;
     d.normal_law = p.normal_law;
+    d.collision = p.collision;
+    d.trt_lambda = (float)p.trt_lambda;
     d.plane = plane_of(nx, ny);
     auto ab = [](double l, double h, float& a, float& b) { a = (float)(0.5 * (l + h)); b = (float)(0.5 * (h - l)); };
     ab(p.rho_l, p.rho_h, d.rho_a, d.rho_b);

@@ -23,8 +23,9 @@ _PARAM_DOUBLES = [
     "u_ave", "phi_in", "T_in", "p_out",
     "T_bot", "T_bot_amp", "T_bot_k", "T_bot_slope", "T_top", "T_top_slope",
     "fp16_scale_f", "fp16_scale_g", "fp16_scale_h",
+    "trt_lambda",
 ]
-_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "storage", "normal_law"]
+_PARAM_INTS = ["sigma_law", "bc_x", "bc_y", "storage", "normal_law", "collision"]
 
 STORAGE_FP32 = 0
 STORAGE_FP16 = 1

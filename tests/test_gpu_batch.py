@@ -117,23 +117,6 @@ def test_tile_shapes_agree_and_tuner_picks_one():
     assert b.t == len(shapes) * 12
 
 
-def test_fp16_batch_matches_single_lattices():
-    """FP16 storage: each member of the batch is bit-identical to the same lattice
-    stepped alone (same tile routine, same reference records)."""
-    from paper_2306_11320_gb300.tpflbm import Lattice
-
-    members = [(nx, ny, dict(p, **WL.fp16_scales(p)), f) for nx, ny, p, f in _members()]
-    b = _batch(members, storage=1)
-    b.step(60)
-    for k, (nx, ny, p, f) in enumerate(members):
-        lat = Lattice(nx, ny, p, storage=1)
-        lat.init(**{n: v.astype(np.float32) for n, v in f.items()})
-        lat.step(60)
-        a, c = b.fields(k), lat.fields()
-        for n in FIELDS:
-            assert np.array_equal(a[n], c[n]), (k, n)
-
-
 def test_fp16_batch():
     """FP16 storage in the batch: within 5e-3 relative L2 of the FP64 oracle, plus three
     times the float32 oracle's own deviation for members whose flow is so weak

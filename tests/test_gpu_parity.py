@@ -197,6 +197,28 @@ def test_local_normal_law(case):
     _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
 
 
+@pytest.mark.parametrize("case", ["random", "random_open", "drop"])
+def test_trt_collision(case):
+    """Two-relaxation-time NS and thermal collisions (collision = 1) against the oracle
+    with the same operator, per-node relaxation times from the phase contrasts."""
+    if case == "random":
+        nx, ny = 96, 48
+        p, f, _ = WL.random_state(nx, ny, seed=11, bc_x=0, bc_y=0, sigma_law=1)
+        steps = 200
+    elif case == "random_open":
+        nx, ny = 64, 32
+        p, f, _ = WL.random_state(nx, ny, seed=12, bc_x=1, bc_y=0, sigma_law=0)
+        steps = 200
+    else:
+        nx, ny = 256, 1024
+        p, f, _ = WL.drop_migration(Ma=10.0)
+        steps = 300
+    p = dict(p, collision=1, trt_lambda=0.25)
+    gpu, orc, o32 = _pair(nx, ny, p, f, floor=True)
+    _run_all((gpu, orc, o32), steps)
+    _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
+
+
 def test_mass_and_diagnostics():
     """FP64 device reductions against the oracle's fields; phi mass conserved in FP32."""
     nx, ny = 96, 64
