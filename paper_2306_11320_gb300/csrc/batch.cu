@@ -33,8 +33,13 @@ constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4};
 
 // Persistent CTAs walk the work list of (instance, tile) pairs; each tile goes
 // through the general tile routine with its instance's parameters and buffers.
+// resident threads per SM the batch kernel is built for: the general tile path is
+// latency-bound, and FP32 at 2 CTAs of 256 threads per SM (107 registers) ran 20% slower
+// than at 3; FP16 keeps 2 (at 80 registers it spills)
+template <class S>
+constexpr int kBatchThreadsPerSM = kRef<S> ? 512 : 768;
 template <int BX, int BY, class S>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, kBatchThreadsPerSM<S> / (BX * BY) > 0 ? kBatchThreadsPerSM<S> / (BX * BY) : 1)
 k_step_batch(const InstDesc* __restrict__ inst, const int2* __restrict__ work, int nwork, int parity)
 {
     __shared__ RingSmem<BX, BY> sm;
