@@ -78,6 +78,21 @@ __device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int 
     return sy * P.nx + sx;
 }
 
+// ref_source for a node of a TMA tile: the writer's slot in the tile's record box
+// (origin x0 - 4, y0 - 2, row length RW).  TMA tiles never need a periodic wrap.
+__device__ __forceinline__ int ref_slot_box(const DevParams& P, int x, int y, int i, bool g_lbe, int x0, int y0,
+                                            int RW)
+{
+    int sx = x - cx(i), sy = y - cy(i);
+    if (sy < 0 || sy >= P.ny || sx < 0 || (sx >= P.nx && g_lbe)) {
+        sx = x;
+        sy = y;
+    } else if (sx >= P.nx) {
+        sx = P.nx - 1;
+    }
+    return (sy - y0 + 2) * RW + sx - x0 + 4;
+}
+
 // Decoded populations of node (x, y) read from global memory (general path).
 template <class S, bool WANT_G = true>
 __device__ __forceinline__ void load_node(const DevParams& P, const typename S::elem* __restrict__ A,
@@ -326,9 +341,13 @@ k_step_general(const DevParams P, const typename S::elem* __restrict__ A, typena
 
 // ------------------------------------------------------------ TMA kernel
 //
-// Persistent CTAs walk a tile list: first the TMA tiles (tile and halo inside the
-// lattice: x0 >= XP, x0 + BX + XP <= nx, y0 >= 2, y0 + BY + 2 <= ny), then the edge
-// tiles through the general path.  For a TMA tile one elected thread issues 3D bulk
+// Persistent CTAs walk a tile list: first the TMA tiles, then the remaining tiles
+// through the general path.  TMA tiles are the whole tiles whose halo lies inside the
+// lattice along each periodic axis (x0 >= XP, x0 + BX + XP <= nx; y0 >= 2,
+// y0 + BY + 2 <= ny), which along a walled or inlet/outflow axis are all whole tiles:
+// there the box reaches past the lattice, the copy fills it with zeros, and the tile
+// takes its ghost ring nodes and its boundary nodes' FP16 records by the boundary
+// rules instead.  For a TMA tile one elected thread issues 3D bulk
 // tensor copies (cp.async.bulk.tensor) of the 9 f planes and the 9 h planes over the
 // tile plus a one-node ring (widened to XP columns each side for the 16-byte rule),
 // the 9 g planes and the 2 (phi u) planes over the tile, and for FP16 the 3 planes of
@@ -408,10 +427,9 @@ struct PhiSmem {
 };
 
 // CTAs per SM the TMA kernel is built for (shared memory allows up to 2 for FP32 and
-// 3 for FP16; more CTAs means fewer registers per thread).  Measured on the 2048 x 512
-// channel: FP32 1 CTA 21.4 GLUPS vs 2 CTAs 20.8; FP16 2 CTAs 17.0 vs 3 CTAs 16.2.
+// 3 for FP16; more CTAs means fewer registers per thread).
 #ifndef TPF_TMA_BLOCKS_F32
-#define TPF_TMA_BLOCKS_F32 1
+#define TPF_TMA_BLOCKS_F32 2
 #endif
 #ifndef TPF_TMA_BLOCKS_F16
 #define TPF_TMA_BLOCKS_F16 2
@@ -449,8 +467,37 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     }
     __syncthreads();
 
+    // Tile list: first the rectangle's rows and columns that touch the lattice boundary
+    // (only its first and last row and column can), then the others row by row, so that
+    // no CTA's round-robin share holds more than one of the slower boundary tiles while
+    // fewer of them than CTAs exist.
+    auto row_edge = [&](int b) { return b * BY <= 1 || b * BY + BY >= P.ny - 1; };
+    auto col_edge = [&](int b) { return b * BX <= 1 || b * BX + BX >= P.nx - 1; };
+    const bool fre = row_edge(by0), lre = ntby > 1 && row_edge(by0 + ntby - 1);
+    const bool fce = col_edge(bx0), lce = ntbx > 1 && col_edge(bx0 + ntbx - 1);
+    const int nr = (int)fre + (int)lre, nc = (int)fce + (int)lce;
+    const int rlo = by0 + (int)fre, nrest = ntby - nr;  // rows that are not boundary rows
+    const int clo = bx0 + (int)fce, ncrest = ntbx - nc;
+    auto tile_of = [&](int t, int& bx, int& by) {
+        if (t < nr * ntbx) {
+            bx = bx0 + t % ntbx;
+            by = (t / ntbx == 0 && fre) ? by0 : by0 + ntby - 1;
+            return;
+        }
+        t -= nr * ntbx;
+        if (t < nc * nrest) {
+            by = rlo + t % nrest;
+            bx = (t / nrest == 0 && fce) ? bx0 : bx0 + ntbx - 1;
+            return;
+        }
+        t -= nc * nrest;
+        bx = clo + t % ncrest;
+        by = rlo + t / ncrest;
+    };
+
     auto issue = [&](int t, int s) {
-        const int bx = bx0 + t % ntbx, by = by0 + t / ntbx;
+        int bx, by;
+        tile_of(t, bx, by);
         const int x0 = bx * BX, y0 = by * BY;
         unsigned char* st = dsm + s * L::STAGE;
         fence_proxy_async();
@@ -472,98 +519,151 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         // every thread waits for the stage itself; a thread whose wait ran out reads
         // stale (in-bounds) shared memory until the block votes at the next barrier
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-        const unsigned char* st = dsm + s * L::STAGE;
-        const E* sF = (const E*)(st + L::OFF_F);
-        const E* sH = (const E*)(st + L::OFF_H);
-        const E* sG = (const E*)(st + L::OFF_G);
-        const float* sU = (const float*)(st + L::OFF_U);
-        const RefT* sR = (const RefT*)(st + L::OFF_R);
-        const int bx = bx0 + t % ntbx, by = by0 + t / ntbx;
+        int bx, by;
+        tile_of(t, bx, by);
         const int x0 = bx * BX, y0 = by * BY;
+        // The tile body, compiled twice: for tiles touching the lattice boundary
+        // (ghost ring nodes, boundary records and pushes) and for all others, which
+        // keep the plain interior code.  Returns true when the block gave up waiting.
+        auto tile = [&](auto edge_c) -> bool {
+            const unsigned char* st = dsm + s * L::STAGE;
+            const E* sF = (const E*)(st + L::OFF_F);
+            const E* sH = (const E*)(st + L::OFF_H);
+            const E* sG = (const E*)(st + L::OFF_G);
+            const float* sU = (const float*)(st + L::OFF_U);
+            const RefT* sR = (const RefT*)(st + L::OFF_R);
+            (void)sR;
+            constexpr bool edge = decltype(edge_c)::value;
+            auto on_boundary = [&](int gx, int gy) { return gx == 0 || gx == P.nx - 1 || gy == 0 || gy == P.ny - 1; };
 
-        // decoded population i of ring slot (lx, ly) from the f (or h) box
-        auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly) {
-            float r = 0.f;
-            if constexpr (kRef<S>) r = ref_pop(i, ref_unpack(sR[(rplane * L::RH + ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i)]));
-            return S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, r);
-        };
-
-        // own node: decoded populations, phi, T, 1/(rho c_p)
-        const int tx = tid % BX, ty = tid / BX;
-        const int lx = tx + 1, ly = ty + 1, kown = ly * SX + lx;
-        const int x = x0 + tx, y = y0 + ty;
-        const int n = y * P.nx + x;
-        float f[9], g[9], h[9], phin[9], Tn[9];
-        {
-            float sf = 0.f, sh = 0.f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                float rf = 0.f, rg = 0.f, rh = 0.f;
-                if constexpr (kRef<S>) {
-                    const int k = (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i);
-                    rf = ref_pop(i, ref_unpack(sR[kRecF * L::RH * L::RW + k]));
-                    rg = ref_g(i, ref_unpack(sR[kRecG * L::RH * L::RW + k]));
-                    rh = ref_pop(i, ref_unpack(sR[kRecH * L::RH * L::RW + k]));
-                }
-                f[i] = S::lds(sF, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_f, rf);
-                h[i] = S::lds(sH, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_h, rh);
-                g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, rg);
-                sf += f[i];
-                sh += h[i];
-            }
-            sm.phi[kown] = sf;
-            sm.T[kown] = sh;
-            sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
-        }
-        // ring: 2 (BX + BY) + 4 nodes, one zeroth moment (f or h) per thread
-        if (tid < 2 * kRing) {
-            const int r = tid < kRing ? tid : tid - kRing;
-            int rx, ry;
-            if (r < SX) { rx = r; ry = 0; }
-            else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
-            else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
-            else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
-            const int k = ry * SX + rx;
-            float s = 0.f;
-            if (tid < kRing) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, kRecF, i, rx, ry);
-                sm.phi[k] = s;
-                sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(s), P.rcp_a));
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, kRecH, i, rx, ry);
-                sm.T[k] = s;
-            }
-        }
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(err, 1);
-                // let this CTA's other copy land (bounded) before leaving
-                if (tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
-            }
-            return;
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int k = kown + cy(i) * SX + cx(i);
-            phin[i] = sm.phi[k];
-            Tn[i] = sm.T[k];
-        }
-        const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
-        phiu[n] = m.phi * m.ux;
-        phiu[pl + n] = m.phi * m.uy;
-        RefVals rown_h{0.f, 0.f, 0.f};
-        if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
-        collide_push<S, SX>(
-            P, B, refB, x, y, kown, true, m, f, g, h,
-            [&](int i, int kd) {
-                // h_i of destination kd came from this node: its reference is this node's record
+            // decoded population i of ring slot (lx, ly) from the f (or h) box
+            auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly, bool bnode) {
                 float r = 0.f;
-                if constexpr (kRef<S>) r = ref_pop(i, rown_h);
-                return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
-            },
-            [&](int kd) { return sm.irc[kd]; });
+                if constexpr (kRef<S>) {
+                    const int k = bnode ? ref_slot_box(P, x0 + lx - 1, y0 + ly - 1, i, false, x0, y0, L::RW)
+                                        : (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i);
+                    r = ref_pop(i, ref_unpack(sR[rplane * L::RH * L::RW + k]));
+                }
+                return S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, r);
+            };
+
+            // own node: decoded populations, phi, T, 1/(rho c_p)
+            const int tx = tid % BX, ty = tid / BX;
+            const int lx = tx + 1, ly = ty + 1, kown = ly * SX + lx;
+            const int x = x0 + tx, y = y0 + ty;
+            const int n = y * P.nx + x;
+            const bool bnode = edge && on_boundary(x, y);
+            float f[9], g[9], h[9], phin[9], Tn[9];
+            {
+                float sf = 0.f, sh = 0.f;
+    #pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    float rf = 0.f, rg = 0.f, rh = 0.f;
+                    if constexpr (kRef<S>) {
+                        int k = (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i), kg = k;
+                        if (bnode) {
+                            k = ref_slot_box(P, x, y, i, false, x0, y0, L::RW);
+                            kg = ref_slot_box(P, x, y, i, true, x0, y0, L::RW);
+                        }
+                        rf = ref_pop(i, ref_unpack(sR[kRecF * L::RH * L::RW + k]));
+                        rg = ref_g(i, ref_unpack(sR[kRecG * L::RH * L::RW + kg]));
+                        rh = ref_pop(i, ref_unpack(sR[kRecH * L::RH * L::RW + k]));
+                    }
+                    f[i] = S::lds(sF, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_f, rf);
+                    h[i] = S::lds(sH, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_h, rh);
+                    g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, rg);
+                    sf += f[i];
+                    sh += h[i];
+                }
+                sm.phi[kown] = sf;
+                sm.T[kown] = sh;
+                sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
+            }
+            // ring: 2 (BX + BY) + 4 nodes, one zeroth moment (f or h) per thread
+            if (tid < 2 * kRing) {
+                const int r = tid < kRing ? tid : tid - kRing;
+                int rx, ry;
+                if (r < SX) { rx = r; ry = 0; }
+                else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
+                else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
+                else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
+                const int k = ry * SX + rx;
+                const int gx = x0 + rx - 1, gy = y0 + ry - 1;
+                const bool ghost = edge && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny);
+                const bool rb = edge && on_boundary(gx, gy);
+                float s = 0.f;
+                if (ghost) {
+                    // filled below from the node it mirrors
+                } else if (tid < kRing) {
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, kRecF, i, rx, ry, rb);
+                    sm.phi[k] = s;
+                    sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(s), P.rcp_a));
+                } else {
+    #pragma unroll
+                    for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, kRecH, i, rx, ry, rb);
+                    sm.T[k] = s;
+                }
+            }
+            if constexpr (edge) {
+                // ghost ring nodes beyond walls, inlet and outflow: phi mirrored, T by the
+                // boundary's rule (as phiT_at does for the general path)
+                __syncthreads();
+                if (tid < kRing) {
+                    const int r = tid;
+                    int rx, ry;
+                    if (r < SX) { rx = r; ry = 0; }
+                    else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
+                    else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
+                    else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
+                    const int gx = x0 + rx - 1, gy = y0 + ry - 1;
+                    const bool ox = gx < 0 || gx >= P.nx, oy = gy < 0 || gy >= P.ny;
+                    if (ox || oy) {
+                        const int mx = ox ? (gx < 0 ? 0 : P.nx - 1) : gx;
+                        const int my = oy ? (gy < 0 ? 0 : P.ny - 1) : gy;
+                        const int km = (my - y0 + 1) * SX + mx - x0 + 1;
+                        const float tm = sm.T[km];
+                        const float tx = (ox && gx < 0) ? 2.f * P.T_in - tm : tm;
+                        const int k = ry * SX + rx;
+                        sm.phi[k] = sm.phi[km];
+                        sm.T[k] = oy ? 2.f * (gy < 0 ? T_wall_bottom(P, (float)gx) : T_wall_top(P, (float)gx)) - tx : tx;
+                        sm.irc[k] = 0.f;
+                    }
+                }
+            }
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicExch(err, 1);
+                    // let this CTA's other copy land (bounded) before leaving
+                    if (tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+                }
+                return true;
+            }
+    #pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int k = kown + cy(i) * SX + cx(i);
+                phin[i] = sm.phi[k];
+                Tn[i] = sm.T[k];
+            }
+            const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
+            phiu[n] = m.phi * m.ux;
+            phiu[pl + n] = m.phi * m.uy;
+            RefVals rown_h{0.f, 0.f, 0.f};
+            (void)rown_h;
+            if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
+            collide_push<S, SX>(
+                P, B, refB, x, y, kown, !edge, m, f, g, h,
+                [&](int i, int kd) {
+                    // h_i of destination kd came from this node: its reference is this node's record
+                    float r = 0.f;
+                    if constexpr (kRef<S>) r = ref_pop(i, rown_h);
+                    return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
+                },
+                [&](int kd) { return sm.irc[kd]; });
+            return false;
+        };
+        const bool edge_tile = x0 <= 1 || x0 + BX >= P.nx - 1 || y0 <= 1 || y0 + BY >= P.ny - 1;
+        if (edge_tile ? tile(std::true_type{}) : tile(std::false_type{})) return;
         __syncthreads();  // stage s and sm are free for the copies issued next iteration
     }
 

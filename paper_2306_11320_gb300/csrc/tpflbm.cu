@@ -545,11 +545,20 @@ void setup_tma(tpflbm_t h)
     const size_t e = sizeof(typename S::elem);
     h->tma = false;
     if (((size_t)nx * e) % 16 != 0 || ((size_t)nx * 4) % 16 != 0) return;
-    // TMA tiles: tile and its (widened) halo inside the lattice
-    const int bx_lo = (L::XP + kBX - 1) / kBX, by_lo = (2 + kBY - 1) / kBY;
-    int bx_hi = -1, by_hi = -1;  // last tile index with x0 + BX + XP <= nx (y0 + BY + 2 <= ny)
-    for (int b = 0; (b + 1) * kBX + L::XP <= nx; ++b) bx_hi = b;
-    for (int b = 0; (b + 1) * kBY + 2 <= ny; ++b) by_hi = b;
+    // TMA tiles: along a periodic axis the tile's (widened) halo inside the lattice;
+    // along a walled or inlet/outflow axis every whole tile (the copies fill the box
+    // beyond the lattice with zeros and the kernel applies the boundary rules there)
+    int bx_lo = 0, by_lo = 0, bx_hi = nx / kBX - 1, by_hi = ny / kBY - 1;
+    if (h->hp.bc_x == 0) {
+        bx_lo = (L::XP + kBX - 1) / kBX;
+        bx_hi = -1;  // last tile index with x0 + BX + XP <= nx
+        for (int b = 0; (b + 1) * kBX + L::XP <= nx; ++b) bx_hi = b;
+    }
+    if (h->hp.bc_y == 1) {
+        by_lo = (2 + kBY - 1) / kBY;
+        by_hi = -1;  // last tile index with y0 + BY + 2 <= ny
+        for (int b = 0; (b + 1) * kBY + 2 <= ny; ++b) by_hi = b;
+    }
     if (bx_hi < bx_lo || by_hi < by_lo) return;
     h->bx0 = bx_lo; h->by0 = by_lo;
     h->ntbx = bx_hi - bx_lo + 1; h->ntby = by_hi - by_lo + 1;
