@@ -295,6 +295,36 @@ def test_fp16_storage(name, steps):
     print(name, steps, errs)
 
 
+@pytest.mark.parametrize("nx,ny,bc_x,bc_y,law", [
+    (128, 40, 1, 0, 1),  # every tile through TMA: inlet, outflow, walls, corners
+    (96, 48, 0, 0, 0),   # TMA tiles along the walls, general tiles at the periodic seam
+    (45, 27, 1, 0, 1),   # general path only
+])
+def test_fp16_two_step_populations(nx, ny, bc_x, bc_y, law):
+    """Two FP16 steps from a random two-phase state, every population against the FP64
+    oracle.  The codec keeps 11 bits of each deviation from its writer's reference, so
+    a correctly decoded population is off by far less than 2^-10 of the field's largest
+    population (2^-8 for g, whose deviations are the largest relative to g itself;
+    measured 2e-5, 2.6e-4 and 6e-5 for f, g and h).  Decoding against the wrong writer's
+    record (a neighbour's, or a zero-filled box entry beyond the lattice) is off by
+    about w_i times the jump in phi or T between nodes, which random states make of
+    order 1e-2 and larger."""
+    from paper_2306_11320_gb300.tpflbm import STORAGE_FP16
+
+    p, f, _ = WL.random_state(nx, ny, seed=nx + 5 * ny, bc_x=bc_x, bc_y=bc_y, sigma_law=law)
+    p = dict(p, **WL.fp16_scales(p))
+    gpu, orc = _pair(nx, ny, p, f, storage=STORAGE_FP16)
+    gpu.step(2)
+    orc.step(2)
+    a, b = gpu.get_state(), orc.get_state()
+    # (phi u) is float32 but formed from decoded populations, so it carries the codec's
+    # error through phi and u: it gets the looser 2^-6
+    for k, tol in (("f", 2.0 ** -10), ("g", 2.0 ** -8), ("h", 2.0 ** -10), ("phiu", 2.0 ** -6)):
+        scale = np.abs(b[k]).max()
+        err = np.abs(a[k] - b[k]).max()
+        assert err <= tol * scale, (k, err, scale)
+
+
 def test_fp16_state_round_trip():
     """set_state / get_state through the float16 codec: each population comes back
     within half a float16 ulp of its scaled deviation from the reference (at most
