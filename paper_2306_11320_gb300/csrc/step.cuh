@@ -230,8 +230,9 @@ __device__ __forceinline__ void collide_push(const DevParams& P, typename S::ele
 }
 
 // One tile through the general path: thread loads, ghost values and every boundary
-// rule.  Used for lattices whose rows do not meet TMA alignment and for the tiles
-// along the lattice edges.  (bx, by): tile coordinates.
+// rule.  Used for lattices whose rows do not meet TMA alignment, by the batched
+// ensemble, and in the TMA kernel for the tiles next to a periodic seam and the ragged
+// tiles.  (bx, by): tile coordinates.
 template <int BX, int BY, class S>
 __device__ __forceinline__ void step_tile_general(const DevParams& P, const typename S::elem* __restrict__ A,
                                                   typename S::elem* __restrict__ B, float* __restrict__ phiu,
@@ -448,7 +449,7 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     constexpr int SX = BX + 2;
     constexpr int kRing = 2 * (BX + BY) + 4;
     static_assert(2 * kRing <= BX * BY, "one thread per ring moment");
-    static_assert(sizeof(RingSmem<BX, BY>) <= 2 * L::STAGE, "edge tiles reuse the stages");
+    static_assert(sizeof(RingSmem<BX, BY>) <= 2 * L::STAGE, "general-path tiles reuse the stages");
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar[2];
     // Where a tile's copies are issued.  FP32: at the top of the tile before, with a
@@ -682,8 +683,9 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
     }
 
-    // edge tiles through the general path, continuing this CTA's round-robin share;
-    // their ring lives in the stages, which the last TMA tile may still be reading
+    // the tiles outside the TMA rectangle (periodic seams, ragged edges) through the
+    // general path, continuing this CTA's round-robin share; their ring lives in the
+    // stages, which the last TMA tile may still be reading
     if (t - ntma < nedge) __syncthreads();
     for (int e = t - ntma; e < nedge; e += gridDim.x) {
         // map edge index e to the e-th tile outside the TMA rectangle
