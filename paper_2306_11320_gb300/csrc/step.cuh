@@ -249,6 +249,31 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
     const int kown = (ty + 1) * SX + tx + 1;
     const bool interior = x0 >= 1 && x0 + BX <= P.nx - 1 && y0 >= 1 && y0 + BY <= P.ny - 1;
 
+    // Whole tiles: one thread per ring node issues that node's loads together with the
+    // own node's, so the tile waits on one round trip to memory, and ghost ring nodes
+    // take their mirror's values from shared memory once those are in.  Ragged tiles
+    // walk every slot outside the lattice part of the tile.
+    constexpr int kRing = 2 * (BX + BY) + 4;
+    static_assert(kRing <= BX * BY, "one thread per ring node");
+    const bool whole = x0 + BX <= P.nx && y0 + BY <= P.ny;
+    int rx = 0, ry = 0, wx = 0, wy = 0;
+    bool rload = false, rghost = false;
+    float ra[9], rc[9];
+    if (whole && (int)threadIdx.x < kRing) {
+        const int r = threadIdx.x;
+        if (r < SX) { rx = r; ry = 0; }
+        else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
+        else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
+        else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
+        wx = x0 + rx - 1;
+        wy = y0 + ry - 1;
+        if (P.bc_x == 0) wx = wrap(wx, P.nx);
+        if (P.bc_y == 1) wy = wrap(wy, P.ny);
+        rload = wx >= 0 && wx < P.nx && wy >= 0 && wy < P.ny;
+        rghost = !rload;
+        if (rload) load_node<S, false>(P, A, refA, wx, wy, ra, nullptr, rc);
+    }
+
     float f[9], g[9], h[9];
     if (active) {
         load_node<S>(P, A, refA, x, y, f, g, h);
@@ -264,52 +289,83 @@ __device__ __forceinline__ void step_tile_general(const DevParams& P, const type
 #pragma unroll
         for (int i = 0; i < 9; ++i) sm.h[i][kown] = h[i];
     }
-    auto get = [&](int gx, int gy, float& ph, float& tt) {
-        float a[9], c[9];
-        load_node<S, false>(P, A, refA, gx, gy, a, nullptr, c);
-        float sf = 0.f, sh = 0.f;
+    if (whole) {
+        if (rload) {
+            const int k = ry * SX + rx;
+            float sf = 0.f, sh = 0.f;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            sf += a[i];
-            sh += c[i];
+            for (int i = 0; i < 9; ++i) {
+                sf += ra[i];
+                sh += rc[i];
+                sm.h[i][k] = rc[i];
+            }
+            sm.phi[k] = sf;
+            sm.T[k] = sh;
+            sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
         }
-        ph = sf;
-        tt = sh;
-    };
-    for (int k = threadIdx.x; k < SN; k += BX * BY) {
-        const int lx = k % SX, ly = k / SX;
-        const bool own = lx >= 1 && lx <= BX && ly >= 1 && ly <= BY && (x0 + lx - 1) < P.nx && (y0 + ly - 1) < P.ny;
-        if (own) continue;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        int wx = gx, wy = gy;
-        if (P.bc_x == 0) wx = wrap(wx, P.nx);
-        if (P.bc_y == 1) wy = wrap(wy, P.ny);
-        const bool far = gx < -1 || gx > P.nx || gy < -1 || gy > P.ny;
-        if (far) {
-            sm.phi[k] = 0.f;
-            sm.T[k] = 0.f;
+        // ghost ring nodes beyond walls, inlet and outflow (as phiT_at): phi mirrored,
+        // T by the boundary's rule; the mirror is the adjacent slot inside the lattice
+        if (__syncthreads_or(rghost) && rghost) {
+            const int gx = x0 + rx - 1, gy = y0 + ry - 1;
+            const int mx = min(max(wx, 0), P.nx - 1), my = min(max(wy, 0), P.ny - 1);
+            const int km = (ry + my - wy) * SX + rx + mx - wx;
+            const float tm = sm.T[km];
+            const float tx = (wx < 0) ? 2.f * P.T_in - tm : tm;
+            const bool oy = wy < 0 || wy >= P.ny;
+            const int k = ry * SX + rx;
+            sm.phi[k] = sm.phi[km];
+            sm.T[k] = oy ? 2.f * (wy < 0 ? T_wall_bottom(P, (float)gx) : T_wall_top(P, (float)gx)) - tx : tx;
             sm.irc[k] = 0.f;
-            continue;
+            (void)gy;
         }
-        if (wx >= 0 && wx < P.nx && wy >= 0 && wy < P.ny) {
+    } else {
+        auto get = [&](int gx, int gy, float& ph, float& tt) {
             float a[9], c[9];
-            load_node<S, false>(P, A, refA, wx, wy, a, nullptr, c);
+            load_node<S, false>(P, A, refA, gx, gy, a, nullptr, c);
             float sf = 0.f, sh = 0.f;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 sf += a[i];
                 sh += c[i];
-                sm.h[i][k] = c[i];
             }
-            sm.phi[k] = sf;
-            sm.T[k] = sh;
-            sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
-        } else {
-            float ph, tt;
-            phiT_at(P, gx, gy, get, ph, tt);
-            sm.phi[k] = ph;
-            sm.T[k] = tt;
-            sm.irc[k] = 0.f;
+            ph = sf;
+            tt = sh;
+        };
+        for (int k = threadIdx.x; k < SN; k += BX * BY) {
+            const int lx = k % SX, ly = k / SX;
+            const bool own = lx >= 1 && lx <= BX && ly >= 1 && ly <= BY && (x0 + lx - 1) < P.nx && (y0 + ly - 1) < P.ny;
+            if (own) continue;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            int qx = gx, qy = gy;
+            if (P.bc_x == 0) qx = wrap(qx, P.nx);
+            if (P.bc_y == 1) qy = wrap(qy, P.ny);
+            const bool far = gx < -1 || gx > P.nx || gy < -1 || gy > P.ny;
+            if (far) {
+                sm.phi[k] = 0.f;
+                sm.T[k] = 0.f;
+                sm.irc[k] = 0.f;
+                continue;
+            }
+            if (qx >= 0 && qx < P.nx && qy >= 0 && qy < P.ny) {
+                float a[9], c[9];
+                load_node<S, false>(P, A, refA, qx, qy, a, nullptr, c);
+                float sf = 0.f, sh = 0.f;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    sf += a[i];
+                    sh += c[i];
+                    sm.h[i][k] = c[i];
+                }
+                sm.phi[k] = sf;
+                sm.T[k] = sh;
+                sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
+            } else {
+                float ph, tt;
+                phiT_at(P, gx, gy, get, ph, tt);
+                sm.phi[k] = ph;
+                sm.T[k] = tt;
+                sm.irc[k] = 0.f;
+            }
         }
     }
     __syncthreads();
