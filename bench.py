@@ -282,7 +282,8 @@ def bench_ours(args, rank, world, local_rank):
 def bench_ensemble(args, rank, world, local_rank):
     """256 independent lattices of 64x64 to 512x256 nodes (microchannel and drop,
     Ma 0.01-50, viscosity and conductivity ratios 0.1-10), one batched launch per
-    step replayed from CUDA graphs, tile shape chosen by the autotuner.  Each rank
+    step replayed from CUDA graphs, variant (tile shape, general or TMA-staged path)
+    chosen by the autotuner.  Each rank
     runs its own copy of the ensemble."""
     import numpy as np
     import torch
@@ -331,7 +332,8 @@ def bench_ensemble(args, rank, world, local_rank):
         "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ensemble_256", "lattices": len(lats), "nodes": nodes, "storage": args.storage,
-                   "tile": "%dx%d" % shapes[best], "tune_ms_per_step": ms,
+                   "tile": "%dx%d" % shapes[best],
+                   "tile_path": "tma" if best == Batch.tma_variant(b.lib) else "general", "tune_ms_per_step": ms,
                    "l2": "state %.0f MB > L2 (steps timed back to back)" % (2 * alg / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,

@@ -237,9 +237,13 @@ const char *tpflbm_last_error(tpflbm_t h);
  * A batch advances n independent lattices (sizes, parameters and boundary kinds may
  * all differ; storage must be the same) together: one persistent launch per time
  * step walks a list of (lattice, tile) pairs and runs the same per-tile step as a
- * single lattice (general tile path); pairs of steps are replayed from a CUDA graph.
- * The tile shape is one of a few compiled shapes (tpflbm_batch_variants), chosen by
- * tpflbm_batch_tune or set directly.  The library allocates every lattice's memory. */
+ * single lattice; pairs of steps are replayed from a CUDA graph.  The variant is one
+ * of a few compiled ones (tpflbm_batch_variants), chosen by tpflbm_batch_tune or set
+ * directly: the general tile path with one of four tile shapes, or (the last
+ * variant) 32 x 8 tiles staged by TMA from each lattice's own tensor maps wherever the
+ * single-lattice kernel would stage them, the rest through the general path.  If a
+ * TMA-staged tile's copies time out, the lattice's next synchronising read-back call
+ * reports TPF_ERR_TIMEOUT.  The library allocates every lattice's memory. */
 typedef struct tpflbm_batch *tpflbm_batch_t;
 
 /* nx[k], ny[k] (3 <= both < 65536) and params[k] of lattice k = 0..n-1.  The batch
@@ -266,15 +270,15 @@ int tpflbm_batch_diagnostics(tpflbm_batch_t b, double *out);
  * 3 doubles per lattice (n x 3).  Synchronises the batch's stream. */
 int tpflbm_batch_residual(tpflbm_batch_t b, const double *dT, double *out);
 
-/* The compiled tile shapes: *count of them, shape v is bx[v] x by[v] nodes (arrays of
- * at least *count entries, or NULL). */
+/* The compiled variants: *count of them, variant v has bx[v] x by[v] node tiles (arrays
+ * of at least *count entries, or NULL).  Variant *count - 1 is the TMA-staged one. */
 int tpflbm_batch_variants(int *count, int *bx, int *by);
-/* Use tile shape v for the following steps. */
+/* Use variant v for the following steps. */
 int tpflbm_batch_set_variant(tpflbm_batch_t b, int v);
-/* Time every tile shape over `steps` (>= 2, rounded down to even) steps of the
- * current state and keep the fastest; ms_per_step[v] (or NULL) receives each shape's
- * time per step, *best (or NULL) the chosen shape.  The batch advances by
- * kinds x (steps + 2) steps. */
+/* Time every variant over `steps` (>= 2, rounded down to even) steps of the current
+ * state and keep the fastest; ms_per_step[v] (or NULL) receives each variant's time
+ * per step, *best (or NULL) the chosen one.  The batch advances by
+ * count x (steps + 2) steps. */
 int tpflbm_batch_tune(tpflbm_batch_t b, int steps, double *ms_per_step, int *best);
 /* Steps taken since creation. */
 long long tpflbm_batch_time(tpflbm_batch_t b);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,10 +27,12 @@ struct InstDesc {
     float* phiu;
 };
 
-// Tile shapes the autotuner chooses from (BX x BY nodes, one thread per node).
-constexpr int kNumVariants = 4;
-constexpr int kVarBX[kNumVariants] = {32, 32, 32, 64};
-constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4};
+// Variants the autotuner chooses from: four tile shapes of the general tile path (BX x
+// BY nodes, one thread per node) and, last, the TMA-staged path with 32 x 8 tiles.
+constexpr int kNumVariants = 5;
+constexpr int kTmaVariant = 4;
+constexpr int kVarBX[kNumVariants] = {32, 32, 32, 64, 32};
+constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4, 8};
 
 // Persistent CTAs walk the work list of (instance, tile) pairs; each tile goes
 // through the general tile routine with its instance's parameters and buffers.
@@ -65,6 +68,166 @@ k_step_batch(const InstDesc* __restrict__ inst, const int2* __restrict__ work, i
     }
 }
 
+// ------------------------------------------------ TMA-staged batch kernel
+//
+// The tiles of every lattice whose rows meet the 16-byte rule and that lie in its TMA
+// rectangle (the single-lattice kernel's) are staged by TMA from that lattice's own
+// tensor maps, double buffered across lattices, and run through the single-lattice
+// kernel's tile body; the lattice's parameters and buffer pointers arrive in the same
+// stage by a bulk copy on the same mbarrier.  The remaining tiles follow through the
+// general tile path.
+
+// What a tile needs of its lattice besides the staged populations (a 16-byte multiple,
+// copied into the stage).
+struct __align__(16) BatchTileDesc {
+    DevParams P;
+    void* pop[2];
+    RefT* ref[2];
+    float* phiu;
+    int* err;
+};
+struct BatchTmaInst {  // aligned as its tensor maps
+    TmaMaps maps[2];      // by parity: the copies of a step at parity p read pop[p]
+    BatchTileDesc d;
+};
+
+constexpr int kTBX = 32, kTBY = 8;  // tile of the TMA-staged batch kernel
+
+template <class S>
+struct BatchLayout {
+    using L = TmaLayout<kTBX, kTBY, S>;
+    static constexpr int OFF_D = L::STAGE;
+    static constexpr int STAGE = L::STAGE + L::rnd((int)sizeof(BatchTileDesc));
+    static constexpr uint32_t TX_BYTES = L::TX_BYTES + (uint32_t)sizeof(BatchTileDesc);
+};
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <class S>
+__global__ void __launch_bounds__(kTBX * kTBY, kTmaMinBlocks<S>)
+k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int2* __restrict__ titem, int nt,
+                 const int2* __restrict__ gitem, int ng, int parity)
+{
+    constexpr int BX = kTBX, BY = kTBY;
+    using L = TmaLayout<BX, BY, S>;
+    using BL = BatchLayout<S>;
+    using E = typename S::elem;
+    static_assert(sizeof(RingSmem<BX, BY>) <= 2 * BL::STAGE, "general-path tiles reuse the stages");
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar[2];
+    // issue placement and staging as in k_step_tma
+    constexpr bool kLate = kRef<S>;
+    __shared__ PhiSmem<BX, BY> smb[kLate ? 2 : 1];
+    __shared__ BatchTileDesc gdesc;  // general-path tiles
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int t, int s) {
+        const int2 item = titem[t];
+        const BatchTmaInst& I = inst[item.x];
+        const TmaMaps& M = I.maps[parity];
+        const int x0 = (item.y & 0xffff) * BX, y0 = (item.y >> 16) * BY;
+        unsigned char* st = dsm + s * BL::STAGE;
+        fence_proxy_async();
+        mbar_expect_tx(&bar[s], BL::TX_BYTES);
+        bulk_load(st + BL::OFF_D, &I.d, (uint32_t)sizeof(BatchTileDesc), &bar[s]);
+        tma_load_3d(st + L::OFF_F, &M.popF, &bar[s], x0 - L::XP, y0 - 1, 0);
+        tma_load_3d(st + L::OFF_H, &M.popF, &bar[s], x0 - L::XP, y0 - 1, 18);
+        tma_load_3d(st + L::OFF_G, &M.popG, &bar[s], x0, y0, 9);
+        tma_load_3d(st + L::OFF_U, &M.phiu, &bar[s], x0, y0, 0);
+        if constexpr (kRef<S>) tma_load_3d(st + L::OFF_R, &M.ref, &bar[s], x0 - 4, y0 - 2, 0);
+    };
+
+    int it = 0;
+    int t = blockIdx.x;
+    int2 cur = t < nt ? titem[t] : make_int2(0, 0);
+    if (t < nt && tid == 0) issue(t, 0);
+    for (; t < nt; t += gridDim.x, ++it) {
+        const int s = it & 1;
+        const int tn = t + gridDim.x;
+        const int2 nxt = tn < nt ? titem[tn] : make_int2(0, 0);
+        if constexpr (!kLate) {
+            if (tn < nt && tid == 0) issue(tn, s ^ 1);
+        }
+        PhiSmem<BX, BY>& sm = smb[kLate ? s : 0];
+        const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
+        const unsigned char* st = dsm + s * BL::STAGE;
+        // the lattice's parameters and buffers, landed with the populations (read before
+        // the block's vote only for shared-memory indices the tile body keeps in range)
+        const BatchTileDesc& D = *reinterpret_cast<const BatchTileDesc*>(st + BL::OFF_D);
+        const DevParams& P = D.P;
+        const int x0 = (cur.y & 0xffff) * BX, y0 = (cur.y >> 16) * BY;
+        auto on_abort = [&]() {
+            if (tid == 0) {
+                atomicExch(inst[cur.x].d.err, 1);
+                mbar_wait_bounded(&bar[s], (it >> 1) & 1);
+                if (!kLate && tn < nt) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+        };
+        auto after_ring = [&]() {
+            if constexpr (kLate) {
+                if (tn < nt && tid == 0) issue(tn, s ^ 1);
+            }
+        };
+        E* B = (E*)D.pop[parity ^ 1];
+        RefT* refB = D.ref[parity ^ 1];
+        const bool edge_tile = x0 <= 1 || x0 + BX >= P.nx - 1 || y0 <= 1 || y0 + BY >= P.ny - 1;
+        if (edge_tile ? tma_tile<BX, BY, S, true>(P, B, D.phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring)
+                      : tma_tile<BX, BY, S, false>(P, B, D.phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring))
+            return;
+        if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
+        cur = nxt;
+    }
+
+    // general-path tiles; their ring lives in the stages, which the last TMA tile may
+    // still be reading
+    if (t - nt < ng) __syncthreads();
+    for (int w = t - nt; w < ng; w += gridDim.x) {
+        const int2 item = gitem[w];
+        if (tid == 0) gdesc = inst[item.x].d;
+        __syncthreads();
+        const DevParams& P = gdesc.P;
+        step_tile_general<BX, BY, S>(P, (const E*)gdesc.pop[parity], (E*)gdesc.pop[parity ^ 1], gdesc.phiu,
+                                     gdesc.ref[parity], gdesc.ref[parity ^ 1],
+                                     *reinterpret_cast<RingSmem<BX, BY>*>(dsm), item.y & 0xffff, item.y >> 16);
+        // step_tile_general ends with a barrier: gdesc is free again
+    }
+}
+
+template <class S>
+void launch_tma(const BatchTmaInst* inst, const int2* work, int nt, int ng, int parity, int grid, cudaStream_t s)
+{
+    k_step_batch_tma<S><<<grid, kTBX * kTBY, 2 * BatchLayout<S>::STAGE, s>>>(inst, work, nt, work + nt, ng, parity);
+}
+
+template <class S>
+int occupancy_tma()
+{
+    const int smem = 2 * BatchLayout<S>::STAGE;
+    if (cudaFuncSetAttribute(k_step_batch_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch_tma<S>, kTBX * kTBY, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
 template <int V, class S>
 void launch_variant(const InstDesc* inst, const int2* work, int nwork, int parity, int grid, cudaStream_t s)
 {
@@ -79,7 +242,8 @@ void launch(int v, const InstDesc* inst, const int2* work, int nwork, int parity
         case 0: launch_variant<0, S>(inst, work, nwork, parity, grid, s); break;
         case 1: launch_variant<1, S>(inst, work, nwork, parity, grid, s); break;
         case 2: launch_variant<2, S>(inst, work, nwork, parity, grid, s); break;
-        default: launch_variant<3, S>(inst, work, nwork, parity, grid, s); break;
+        case 3: launch_variant<3, S>(inst, work, nwork, parity, grid, s); break;
+        default: break;  // kTmaVariant: launch_tma
     }
 }
 
@@ -102,7 +266,8 @@ int occupancy(int v)
         case 0: return occupancy_variant<0, S>();
         case 1: return occupancy_variant<1, S>();
         case 2: return occupancy_variant<2, S>();
-        default: return occupancy_variant<3, S>();
+        case 3: return occupancy_variant<3, S>();
+        default: return std::max(1, occupancy_tma<S>());
     }
 }
 
@@ -114,6 +279,8 @@ struct tpflbm_batch {
     int num_sms = 0;
     std::vector<tpflbm_t> inst;
     InstDesc* d_inst = nullptr;
+    BatchTmaInst* d_tinst = nullptr;  // TMA-staged variant: per-lattice maps and descriptors
+    int ntma = 0;                     // its TMA items (the first ntma of d_work[kTmaVariant])
     int2* d_work[kNumVariants] = {};
     int nwork[kNumVariants] = {};
     int grid[kNumVariants] = {};
@@ -145,6 +312,14 @@ int bfail(tpflbm_batch_t b, int code, const std::string& msg)
 
 void launch_batch(tpflbm_batch_t b, int v, int parity)
 {
+    if (v == kTmaVariant) {
+        const int ng = b->nwork[v] - b->ntma;
+        if (b->storage == TPF_STORAGE_FP16)
+            launch_tma<StoreF16>(b->d_tinst, b->d_work[v], b->ntma, ng, parity, b->grid[v], b->stream);
+        else
+            launch_tma<StoreF32>(b->d_tinst, b->d_work[v], b->ntma, ng, parity, b->grid[v], b->stream);
+        return;
+    }
     if (b->storage == TPF_STORAGE_FP16)
         launch<StoreF16>(v, b->d_inst, b->d_work[v], b->nwork[v], parity, b->grid[v], b->stream);
     else
@@ -228,6 +403,26 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
     }
     cudaError_t e = cudaMalloc(&b->d_inst, n * sizeof(InstDesc));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice);
+    // the TMA-staged variant: each lattice's own tensor maps (built by its handle when its
+    // rows meet the 16-byte rule) and descriptor
+    std::vector<BatchTmaInst> tdesc(n);
+    for (int k = 0; k < n; ++k) {
+        tpflbm_t h = b->inst[k];
+        std::memset(&tdesc[k], 0, sizeof(BatchTmaInst));
+        if (h->tma) {
+            tdesc[k].maps[0] = h->maps[0];
+            tdesc[k].maps[1] = h->maps[1];
+        }
+        tdesc[k].d.P = h->dp;
+        tdesc[k].d.pop[0] = h->pop[0];
+        tdesc[k].d.pop[1] = h->pop[1];
+        tdesc[k].d.ref[0] = h->ref[0];
+        tdesc[k].d.ref[1] = h->ref[1];
+        tdesc[k].d.phiu = h->phiu;
+        tdesc[k].d.err = h->err;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tinst, n * sizeof(BatchTmaInst));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tinst, tdesc.data(), n * sizeof(BatchTmaInst), cudaMemcpyHostToDevice);
     for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
         std::vector<int2> work;
         const int BX = kVarBX[v], BY = kVarBY[v];
@@ -241,9 +436,43 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
             total += (long long)tx[k] * ty[k];
         }
         work.reserve(total);
-        for (int k = 0; k < n; ++k)
-            for (int by = 0; by < ty[k]; ++by)
-                for (int bx = 0; bx < tx[k]; ++bx) work.push_back(make_int2(k, bx | (by << 16)));
+        if (v == kTmaVariant) {
+            // TMA items first: every lattice's boundary tiles, then its other tiles, each
+            // group interleaved over the lattices (at most one boundary tile per CTA while
+            // there are fewer of them than CTAs); then the general-path items
+            std::vector<std::vector<int2>> edge(n), inner(n), rest(n);
+            for (int k = 0; k < n; ++k) {
+                tpflbm_t h = b->inst[k];
+                for (int by = 0; by < ty[k]; ++by)
+                    for (int bx = 0; bx < tx[k]; ++bx) {
+                        const int2 it = make_int2(k, bx | (by << 16));
+                        const bool in = h->tma && bx >= h->bx0 && bx < h->bx0 + h->ntbx && by >= h->by0 &&
+                                        by < h->by0 + h->ntby;
+                        if (!in) {
+                            rest[k].push_back(it);
+                            continue;
+                        }
+                        const int x0 = bx * BX, y0 = by * BY;
+                        const bool eg = x0 <= 1 || x0 + BX >= nx[k] - 1 || y0 <= 1 || y0 + BY >= ny[k] - 1;
+                        (eg ? edge[k] : inner[k]).push_back(it);
+                    }
+            }
+            auto interleave = [&](std::vector<std::vector<int2>>& lists) {
+                size_t most = 0;
+                for (auto& l : lists) most = std::max(most, l.size());
+                for (size_t i = 0; i < most; ++i)
+                    for (auto& l : lists)
+                        if (i < l.size()) work.push_back(l[i]);
+            };
+            interleave(edge);
+            interleave(inner);
+            b->ntma = (int)work.size();
+            interleave(rest);
+        } else {
+            for (int k = 0; k < n; ++k)
+                for (int by = 0; by < ty[k]; ++by)
+                    for (int bx = 0; bx < tx[k]; ++bx) work.push_back(make_int2(k, bx | (by << 16)));
+        }
         b->nwork[v] = (int)work.size();
         if (b->storage == TPF_STORAGE_FP16) b->grid[v] = occupancy<StoreF16>(v) * b->num_sms;
         else b->grid[v] = occupancy<StoreF32>(v) * b->num_sms;
@@ -415,6 +644,7 @@ void tpflbm_batch_destroy(tpflbm_batch_t b)
     }
     for (int v = 0; v < kNumVariants; ++v) cudaFree(b->d_work[v]);
     cudaFree(b->d_inst);
+    cudaFree(b->d_tinst);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -79,9 +79,11 @@ __device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int 
 }
 
 // ref_source for a node of a TMA tile: the writer's slot in the tile's record box
-// (origin x0 - 4, y0 - 2, row length RW).  TMA tiles never need a periodic wrap.
+// (origin x0 - 4, y0 - 2, RW x RH).  TMA tiles never need a periodic wrap.  Every
+// writer lies in the box; the clamps only keep the slot inside it when P itself is not
+// to be trusted (a batched tile whose copies, parameters included, timed out).
 __device__ __forceinline__ int ref_slot_box(const DevParams& P, int x, int y, int i, bool g_lbe, int x0, int y0,
-                                            int RW)
+                                            int RW, int RH)
 {
     int sx = x - cx(i), sy = y - cy(i);
     if (sy < 0 || sy >= P.ny || sx < 0 || (sx >= P.nx && g_lbe)) {
@@ -90,7 +92,8 @@ __device__ __forceinline__ int ref_slot_box(const DevParams& P, int x, int y, in
     } else if (sx >= P.nx) {
         sx = P.nx - 1;
     }
-    return (sy - y0 + 2) * RW + sx - x0 + 4;
+    const int c = min(max(sx - x0 + 4, 0), RW - 1), r = min(max(sy - y0 + 2, 0), RH - 1);
+    return r * RW + c;
 }
 
 // Decoded populations of node (x, y) read from global memory (general path).
@@ -483,6 +486,160 @@ struct PhiSmem {
     float irc[SN];
 };
 
+// The body of one TMA tile, shared by the single-lattice and the batched kernels: decode
+// the staged populations of the tile (stage st, landed unless ok is false) and its
+// ring, phi / T / 1/(rho c_p) into sm, one block barrier (which also votes on ok:
+// on_abort() runs on every thread and the tile returns true when any wait ran out),
+// after_ring() on every thread, then per node the macroscopic state, the collisions
+// and the push to B.  EDGE: the tile touches the lattice boundary (ghost ring nodes,
+// boundary records, boundary-aware push for every node).
+template <int BX, int BY, class S, bool EDGE, class OnAbort, class AfterRing>
+__device__ __forceinline__ bool tma_tile(const DevParams& P, typename S::elem* __restrict__ B,
+                                         float* __restrict__ phiu, RefT* __restrict__ refB,
+                                         const unsigned char* st, PhiSmem<BX, BY>& sm, int x0, int y0, bool ok,
+                                         OnAbort on_abort, AfterRing after_ring)
+{
+    using L = TmaLayout<BX, BY, S>;
+    using E = typename S::elem;
+    constexpr int SX = BX + 2;
+    constexpr int kRing = 2 * (BX + BY) + 4;
+    static_assert(2 * kRing <= BX * BY, "one thread per ring moment");
+    const int tid = threadIdx.x;
+    const long long pl = P.plane;
+    const E* sF = (const E*)(st + L::OFF_F);
+    const E* sH = (const E*)(st + L::OFF_H);
+    const E* sG = (const E*)(st + L::OFF_G);
+    const float* sU = (const float*)(st + L::OFF_U);
+    const RefT* sR = (const RefT*)(st + L::OFF_R);
+    (void)sR;
+    constexpr bool edge = EDGE;
+    auto on_boundary = [&](int gx, int gy) { return gx == 0 || gx == P.nx - 1 || gy == 0 || gy == P.ny - 1; };
+
+    // decoded population i of ring slot (lx, ly) from the f (or h) box
+    auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly, bool bnode) {
+        float r = 0.f;
+        if constexpr (kRef<S>) {
+            const int k = bnode ? ref_slot_box(P, x0 + lx - 1, y0 + ly - 1, i, false, x0, y0, L::RW, L::RH)
+                                : (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i);
+            r = ref_pop(i, ref_unpack(sR[rplane * L::RH * L::RW + k]));
+        }
+        return S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, r);
+    };
+
+    // own node: decoded populations, phi, T, 1/(rho c_p)
+    const int tx = tid % BX, ty = tid / BX;
+    const int lx = tx + 1, ly = ty + 1, kown = ly * SX + lx;
+    const int x = x0 + tx, y = y0 + ty;
+    const int n = y * P.nx + x;
+    const bool bnode = edge && on_boundary(x, y);
+    float f[9], g[9], h[9], phin[9], Tn[9];
+    {
+        float sf = 0.f, sh = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float rf = 0.f, rg = 0.f, rh = 0.f;
+            if constexpr (kRef<S>) {
+                int k = (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i), kg = k;
+                if (bnode) {
+                    k = ref_slot_box(P, x, y, i, false, x0, y0, L::RW, L::RH);
+                    kg = ref_slot_box(P, x, y, i, true, x0, y0, L::RW, L::RH);
+                }
+                rf = ref_pop(i, ref_unpack(sR[kRecF * L::RH * L::RW + k]));
+                rg = ref_g(i, ref_unpack(sR[kRecG * L::RH * L::RW + kg]));
+                rh = ref_pop(i, ref_unpack(sR[kRecH * L::RH * L::RW + k]));
+            }
+            f[i] = S::lds(sF, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_f, rf);
+            h[i] = S::lds(sH, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_h, rh);
+            g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, rg);
+            sf += f[i];
+            sh += h[i];
+        }
+        sm.phi[kown] = sf;
+        sm.T[kown] = sh;
+        sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
+    }
+    // ring: 2 (BX + BY) + 4 nodes, one zeroth moment (f or h) per thread
+    if (tid < 2 * kRing) {
+        const int r = tid < kRing ? tid : tid - kRing;
+        int rx, ry;
+        if (r < SX) { rx = r; ry = 0; }
+        else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
+        else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
+        else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
+        const int k = ry * SX + rx;
+        const int gx = x0 + rx - 1, gy = y0 + ry - 1;
+        const bool ghost = edge && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny);
+        const bool rb = edge && on_boundary(gx, gy);
+        float s = 0.f;
+        if (ghost) {
+            // filled below from the node it mirrors
+        } else if (tid < kRing) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, kRecF, i, rx, ry, rb);
+            sm.phi[k] = s;
+            sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(s), P.rcp_a));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, kRecH, i, rx, ry, rb);
+            sm.T[k] = s;
+        }
+    }
+    if constexpr (edge) {
+        // ghost ring nodes beyond walls, inlet and outflow: phi mirrored, T by the
+        // boundary's rule (as phiT_at does for the general path)
+        __syncthreads();
+        if (tid < kRing) {
+            const int r = tid;
+            int rx, ry;
+            if (r < SX) { rx = r; ry = 0; }
+            else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
+            else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
+            else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
+            const int gx = x0 + rx - 1, gy = y0 + ry - 1;
+            const bool ox = gx < 0 || gx >= P.nx, oy = gy < 0 || gy >= P.ny;
+            if (ox || oy) {
+                const int mx = ox ? (gx < 0 ? 0 : P.nx - 1) : gx;
+                const int my = oy ? (gy < 0 ? 0 : P.ny - 1) : gy;
+                // (the clamp only matters when P is not to be trusted, as above)
+                const int km = min(max((my - y0 + 1) * SX + mx - x0 + 1, 0), PhiSmem<BX, BY>::SN - 1);
+                const float tm = sm.T[km];
+                const float tx = (ox && gx < 0) ? 2.f * P.T_in - tm : tm;
+                const int k = ry * SX + rx;
+                sm.phi[k] = sm.phi[km];
+                sm.T[k] = oy ? 2.f * (gy < 0 ? T_wall_bottom(P, (float)gx) : T_wall_top(P, (float)gx)) - tx : tx;
+                sm.irc[k] = 0.f;
+            }
+        }
+    }
+    if (__syncthreads_or(!ok)) {
+        on_abort();
+        return true;
+    }
+    after_ring();
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int k = kown + cy(i) * SX + cx(i);
+        phin[i] = sm.phi[k];
+        Tn[i] = sm.T[k];
+    }
+    const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
+    phiu[n] = m.phi * m.ux;
+    phiu[pl + n] = m.phi * m.uy;
+    RefVals rown_h{0.f, 0.f, 0.f};
+    (void)rown_h;
+    if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
+    collide_push<S, SX>(
+        P, B, refB, x, y, kown, !edge, m, f, g, h,
+        [&](int i, int kd) {
+            // h_i of destination kd came from this node: its reference is this node's record
+            float r = 0.f;
+            if constexpr (kRef<S>) r = ref_pop(i, rown_h);
+            return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
+        },
+        [&](int kd) { return sm.irc[kd]; });
+    return false;
+}
+
 // CTAs per SM the TMA kernel is built for (shared memory allows up to 2 for FP32 and
 // 3 for FP16; more CTAs means fewer registers per thread).
 #ifndef TPF_TMA_BLOCKS_F32
@@ -501,10 +658,6 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
            RefT* __restrict__ refB, int bx0, int by0, int ntbx, int ntby, int* __restrict__ err)
 {
     using L = TmaLayout<BX, BY, S>;
-    using E = typename S::elem;
-    constexpr int SX = BX + 2;
-    constexpr int kRing = 2 * (BX + BY) + 4;
-    static_assert(2 * kRing <= BX * BY, "one thread per ring moment");
     static_assert(sizeof(RingSmem<BX, BY>) <= 2 * L::STAGE, "general-path tiles reuse the stages");
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -522,7 +675,6 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     const int nall = tilesx * tilesy;
     const int nedge = nall - ntma;
     const int tid = threadIdx.x;
-    const long long pl = P.plane;
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -589,153 +741,27 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         int bx, by;
         tile_of(t, bx, by);
         const int x0 = bx * BX, y0 = by * BY;
-        // The tile body, compiled twice: for tiles touching the lattice boundary
-        // (ghost ring nodes, boundary records and pushes) and for all others, which
-        // keep the plain interior code.  Returns true when the block gave up waiting.
-        auto tile = [&](auto edge_c) -> bool {
-            const unsigned char* st = dsm + s * L::STAGE;
-            const E* sF = (const E*)(st + L::OFF_F);
-            const E* sH = (const E*)(st + L::OFF_H);
-            const E* sG = (const E*)(st + L::OFF_G);
-            const float* sU = (const float*)(st + L::OFF_U);
-            const RefT* sR = (const RefT*)(st + L::OFF_R);
-            (void)sR;
-            constexpr bool edge = decltype(edge_c)::value;
-            auto on_boundary = [&](int gx, int gy) { return gx == 0 || gx == P.nx - 1 || gy == 0 || gy == P.ny - 1; };
-
-            // decoded population i of ring slot (lx, ly) from the f (or h) box
-            auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly, bool bnode) {
-                float r = 0.f;
-                if constexpr (kRef<S>) {
-                    const int k = bnode ? ref_slot_box(P, x0 + lx - 1, y0 + ly - 1, i, false, x0, y0, L::RW)
-                                        : (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i);
-                    r = ref_pop(i, ref_unpack(sR[rplane * L::RH * L::RW + k]));
-                }
-                return S::lds(box, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, is, r);
-            };
-
-            // own node: decoded populations, phi, T, 1/(rho c_p)
-            const int tx = tid % BX, ty = tid / BX;
-            const int lx = tx + 1, ly = ty + 1, kown = ly * SX + lx;
-            const int x = x0 + tx, y = y0 + ty;
-            const int n = y * P.nx + x;
-            const bool bnode = edge && on_boundary(x, y);
-            float f[9], g[9], h[9], phin[9], Tn[9];
-            {
-                float sf = 0.f, sh = 0.f;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    float rf = 0.f, rg = 0.f, rh = 0.f;
-                    if constexpr (kRef<S>) {
-                        int k = (ly + 1 - cy(i)) * L::RW + lx + 3 - cx(i), kg = k;
-                        if (bnode) {
-                            k = ref_slot_box(P, x, y, i, false, x0, y0, L::RW);
-                            kg = ref_slot_box(P, x, y, i, true, x0, y0, L::RW);
-                        }
-                        rf = ref_pop(i, ref_unpack(sR[kRecF * L::RH * L::RW + k]));
-                        rg = ref_g(i, ref_unpack(sR[kRecG * L::RH * L::RW + kg]));
-                        rh = ref_pop(i, ref_unpack(sR[kRecH * L::RH * L::RW + k]));
-                    }
-                    f[i] = S::lds(sF, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_f, rf);
-                    h[i] = S::lds(sH, (i * L::FH + ly) * L::FW + lx - 1 + L::XP, P.is_h, rh);
-                    g[i] = S::lds(sG, (i * BY + ty) * BX + tx, P.is_g, rg);
-                    sf += f[i];
-                    sh += h[i];
-                }
-                sm.phi[kown] = sf;
-                sm.T[kown] = sh;
-                sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
+        // the tile body is compiled twice: for tiles touching the lattice boundary and
+        // for all others, which keep the plain interior code
+        auto on_abort = [&]() {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // let this CTA's copies in flight land (bounded) before leaving
+                mbar_wait_bounded(&bar[s], (it >> 1) & 1);
+                if (!kLate && tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
             }
-            // ring: 2 (BX + BY) + 4 nodes, one zeroth moment (f or h) per thread
-            if (tid < 2 * kRing) {
-                const int r = tid < kRing ? tid : tid - kRing;
-                int rx, ry;
-                if (r < SX) { rx = r; ry = 0; }
-                else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
-                else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
-                else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
-                const int k = ry * SX + rx;
-                const int gx = x0 + rx - 1, gy = y0 + ry - 1;
-                const bool ghost = edge && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny);
-                const bool rb = edge && on_boundary(gx, gy);
-                float s = 0.f;
-                if (ghost) {
-                    // filled below from the node it mirrors
-                } else if (tid < kRing) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) s += decF(sF, P.is_f, kRecF, i, rx, ry, rb);
-                    sm.phi[k] = s;
-                    sm.irc[k] = __frcp_rn(fmaf(P.rcp_b, clamp1(s), P.rcp_a));
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) s += decF(sH, P.is_h, kRecH, i, rx, ry, rb);
-                    sm.T[k] = s;
-                }
-            }
-            if constexpr (edge) {
-                // ghost ring nodes beyond walls, inlet and outflow: phi mirrored, T by the
-                // boundary's rule (as phiT_at does for the general path)
-                __syncthreads();
-                if (tid < kRing) {
-                    const int r = tid;
-                    int rx, ry;
-                    if (r < SX) { rx = r; ry = 0; }
-                    else if (r < 2 * SX) { rx = r - SX; ry = BY + 1; }
-                    else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
-                    else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
-                    const int gx = x0 + rx - 1, gy = y0 + ry - 1;
-                    const bool ox = gx < 0 || gx >= P.nx, oy = gy < 0 || gy >= P.ny;
-                    if (ox || oy) {
-                        const int mx = ox ? (gx < 0 ? 0 : P.nx - 1) : gx;
-                        const int my = oy ? (gy < 0 ? 0 : P.ny - 1) : gy;
-                        const int km = (my - y0 + 1) * SX + mx - x0 + 1;
-                        const float tm = sm.T[km];
-                        const float tx = (ox && gx < 0) ? 2.f * P.T_in - tm : tm;
-                        const int k = ry * SX + rx;
-                        sm.phi[k] = sm.phi[km];
-                        sm.T[k] = oy ? 2.f * (gy < 0 ? T_wall_bottom(P, (float)gx) : T_wall_top(P, (float)gx)) - tx : tx;
-                        sm.irc[k] = 0.f;
-                    }
-                }
-            }
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicExch(err, 1);
-                    // let this CTA's copies in flight land (bounded) before leaving
-                    mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-                    if (!kLate && tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
-                }
-                return true;
-            }
+        };
+        auto after_ring = [&]() {
             if constexpr (kLate) {
                 // every warp has finished the tile before, whose stage is s ^ 1
                 if (tn < ntma && tid == 0) issue(tn, s ^ 1);
             }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int k = kown + cy(i) * SX + cx(i);
-                phin[i] = sm.phi[k];
-                Tn[i] = sm.T[k];
-            }
-            const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
-            phiu[n] = m.phi * m.ux;
-            phiu[pl + n] = m.phi * m.uy;
-            RefVals rown_h{0.f, 0.f, 0.f};
-            (void)rown_h;
-            if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
-            collide_push<S, SX>(
-                P, B, refB, x, y, kown, !edge, m, f, g, h,
-                [&](int i, int kd) {
-                    // h_i of destination kd came from this node: its reference is this node's record
-                    float r = 0.f;
-                    if constexpr (kRef<S>) r = ref_pop(i, rown_h);
-                    return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
-                },
-                [&](int kd) { return sm.irc[kd]; });
-            return false;
         };
+        const unsigned char* st = dsm + s * L::STAGE;
         const bool edge_tile = x0 <= 1 || x0 + BX >= P.nx - 1 || y0 <= 1 || y0 + BY >= P.ny - 1;
-        if (edge_tile ? tile(std::true_type{}) : tile(std::false_type{})) return;
+        if (edge_tile ? tma_tile<BX, BY, S, true>(P, B, phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring)
+                      : tma_tile<BX, BY, S, false>(P, B, phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring))
+            return;
         if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
     }
 

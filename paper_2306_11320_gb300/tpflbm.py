@@ -345,6 +345,11 @@ class Batch:
         lib.tpflbm_batch_variants(C.byref(cnt), bx, by)
         return list(zip(bx[:], by[:]))
 
+    @staticmethod
+    def tma_variant(lib=None):
+        """Index of the TMA-staged variant (the last one)."""
+        return len(Batch.variants(lib)) - 1
+
     def set_variant(self, v: int):
         self._check(self.lib.tpflbm_batch_set_variant(self.h, int(v)))
 

@@ -24,28 +24,35 @@ def _members():
     conductivity ratios) plus random two-phase states with every boundary kind."""
     out = [(m["nx"], m["ny"], p, f) for p, f, m in WL.ensemble(n=6, seed=3, nx_range=(32, 96),
                                                                ny_range=(24, 64))]
-    for (nx, ny, bx, by, law, seed) in ((41, 19, 1, 0, 1, 1), (64, 32, 0, 1, 0, 2), (37, 23, 0, 0, 1, 3)):
+    # the last two run through TMA in the TMA-staged variant: every tile of the inlet /
+    # outflow channel, the walled rows of the periodic lattice
+    for (nx, ny, bx, by, law, seed) in ((41, 19, 1, 0, 1, 1), (64, 32, 0, 1, 0, 2), (37, 23, 0, 0, 1, 3),
+                                        (128, 40, 1, 0, 1, 4), (96, 48, 0, 0, 0, 5)):
         p, f, _ = WL.random_state(nx, ny, seed=seed, bc_x=bx, bc_y=by, sigma_law=law)
         out.append((nx, ny, p, f))
     return out
 
 
-def _batch(members, storage=0):
+def _batch(members, storage=0, variant=None):
     from paper_2306_11320_gb300.tpflbm import Batch
 
     b = Batch([(nx, ny, p) for nx, ny, p, _ in members], storage=storage)
     for k, (_, _, _, f) in enumerate(members):
         b.init(k, **{n: v.astype(np.float32) for n, v in f.items()})
+    if variant == "tma":
+        b.set_variant(Batch.tma_variant(b.lib))
     return b
 
 
-def test_batch_matches_single_lattices():
-    """Each member of the batch evolves exactly as the same lattice stepped alone
-    through the single-lattice API (the per-tile code is shared)."""
+@pytest.mark.parametrize("variant", [None, "tma"])
+def test_batch_matches_single_lattices(variant):
+    """Each member of the batch evolves as the same lattice stepped alone through the
+    single-lattice API (the per-tile code is shared), with the general tile path and
+    with the TMA-staged variant."""
     from paper_2306_11320_gb300.tpflbm import Lattice
 
     members = _members()
-    b = _batch(members)
+    b = _batch(members, variant=variant)
     b.step(40)
     for k, (nx, ny, p, f) in enumerate(members):
         lat = Lattice(nx, ny, p)
@@ -117,13 +124,15 @@ def test_tile_shapes_agree_and_tuner_picks_one():
     assert b.t == len(shapes) * 12
 
 
-def test_fp16_batch():
-    """FP16 storage in the batch: within 5e-3 relative L2 of the FP64 oracle, plus three
-    times the float32 oracle's own deviation for members whose flow is so weak
-    (|u| ~ 1e-7) that float32 arithmetic alone is off by more than that."""
+@pytest.mark.parametrize("variant", [None, "tma"])
+def test_fp16_batch(variant):
+    """FP16 storage in the batch (general tile path, and the TMA-staged variant): within
+    5e-3 relative L2 of the FP64 oracle, plus three times the float32 oracle's own
+    deviation for members whose flow is so weak (|u| ~ 1e-7) that float32 arithmetic
+    alone is off by more than that."""
     members = [m for m in _members()]
     members = [(nx, ny, dict(p, **WL.fp16_scales(p)), f) for nx, ny, p, f in members]
-    b = _batch(members, storage=1)
+    b = _batch(members, storage=1, variant=variant)
     steps = 1500
     b.step(steps)
     for k, (nx, ny, p, f) in enumerate(members):
