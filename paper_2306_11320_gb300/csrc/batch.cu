@@ -98,8 +98,12 @@ struct BatchLayout {
     using L = TmaLayout<kTBX, kTBY, S>;
     static constexpr int OFF_D = L::STAGE;
     static constexpr int STAGE = L::STAGE + L::rnd((int)sizeof(BatchTileDesc));
-    static constexpr uint32_t TX_BYTES = L::TX_BYTES + (uint32_t)sizeof(BatchTileDesc);
 };
+
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
@@ -111,7 +115,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 
 template <class S>
 __global__ void __launch_bounds__(kTBX * kTBY, kTmaMinBlocks<S>)
-k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int2* __restrict__ titem, int nt,
+k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int4* __restrict__ titem, int nt,
                  const int2* __restrict__ gitem, int ng, int parity)
 {
     constexpr int BX = kTBX, BY = kTBY;
@@ -135,35 +139,34 @@ k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int2* __restrict__
     __syncthreads();
 
     auto issue = [&](int t, int s) {
-        const int2 item = titem[t];
+        // item: lattice, tile (bx | by << 16), seam side, boundary tile
+        const int4 item = titem[t];
         const BatchTmaInst& I = inst[item.x];
         const TmaMaps& M = I.maps[parity];
         const int x0 = (item.y & 0xffff) * BX, y0 = (item.y >> 16) * BY;
         unsigned char* st = dsm + s * BL::STAGE;
+        // the descriptor's bytes join the tile's on the same mbarrier (expected without an
+        // arrival; the tile's copies bring the one arrival)
         fence_proxy_async();
-        mbar_expect_tx(&bar[s], BL::TX_BYTES);
+        mbar_expect_tx_only(&bar[s], (uint32_t)sizeof(BatchTileDesc));
         bulk_load(st + BL::OFF_D, &I.d, (uint32_t)sizeof(BatchTileDesc), &bar[s]);
-        tma_load_3d(st + L::OFF_F, &M.popF, &bar[s], x0 - L::XP, y0 - 1, 0);
-        tma_load_3d(st + L::OFF_H, &M.popF, &bar[s], x0 - L::XP, y0 - 1, 18);
-        tma_load_3d(st + L::OFF_G, &M.popG, &bar[s], x0, y0, 9);
-        tma_load_3d(st + L::OFF_U, &M.phiu, &bar[s], x0, y0, 0);
-        if constexpr (kRef<S>) tma_load_3d(st + L::OFF_R, &M.ref, &bar[s], x0 - 4, y0 - 2, 0);
+        tma_issue_tile<BX, BY, S>(M, st, &bar[s], x0, y0);
     };
 
     int it = 0;
     int t = blockIdx.x;
-    int2 cur = t < nt ? titem[t] : make_int2(0, 0);
+    int4 cur = t < nt ? titem[t] : make_int4(0, 0, 0, 0);
     if (t < nt && tid == 0) issue(t, 0);
     for (; t < nt; t += gridDim.x, ++it) {
         const int s = it & 1;
         const int tn = t + gridDim.x;
-        const int2 nxt = tn < nt ? titem[tn] : make_int2(0, 0);
+        const int4 nxt = tn < nt ? titem[tn] : make_int4(0, 0, 0, 0);
         if constexpr (!kLate) {
             if (tn < nt && tid == 0) issue(tn, s ^ 1);
         }
         PhiSmem<BX, BY>& sm = smb[kLate ? s : 0];
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-        const unsigned char* st = dsm + s * BL::STAGE;
+        unsigned char* st = dsm + s * BL::STAGE;
         // the lattice's parameters and buffers, landed with the populations (read before
         // the block's vote only for shared-memory indices the tile body keeps in range)
         const BatchTileDesc& D = *reinterpret_cast<const BatchTileDesc*>(st + BL::OFF_D);
@@ -181,11 +184,15 @@ k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int2* __restrict__
                 if (tn < nt && tid == 0) issue(tn, s ^ 1);
             }
         };
+        // the buffers are read only after the block's vote; which body runs and whether the
+        // seam patch does come from the work item, the same on every thread
+        const E* A = (const E*)D.pop[parity];
         E* B = (E*)D.pop[parity ^ 1];
         RefT* refB = D.ref[parity ^ 1];
-        const bool edge_tile = x0 <= 1 || x0 + BX >= P.nx - 1 || y0 <= 1 || y0 + BY >= P.ny - 1;
-        if (edge_tile ? tma_tile<BX, BY, S, true>(P, B, D.phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring)
-                      : tma_tile<BX, BY, S, false>(P, B, D.phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring))
+        if (cur.w ? tma_tile<BX, BY, S, true>(P, A, B, D.phiu, refB, st, sm, x0, y0, cur.z, ok, on_abort,
+                                              after_ring)
+                  : tma_tile<BX, BY, S, false>(P, A, B, D.phiu, refB, st, sm, x0, y0, 0, ok, on_abort,
+                                               after_ring))
             return;
         if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
         cur = nxt;
@@ -207,9 +214,10 @@ k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int2* __restrict__
 }
 
 template <class S>
-void launch_tma(const BatchTmaInst* inst, const int2* work, int nt, int ng, int parity, int grid, cudaStream_t s)
+void launch_tma(const BatchTmaInst* inst, const int4* titem, int nt, const int2* gitem, int ng, int parity, int grid,
+                cudaStream_t s)
 {
-    k_step_batch_tma<S><<<grid, kTBX * kTBY, 2 * BatchLayout<S>::STAGE, s>>>(inst, work, nt, work + nt, ng, parity);
+    k_step_batch_tma<S><<<grid, kTBX * kTBY, 2 * BatchLayout<S>::STAGE, s>>>(inst, titem, nt, gitem, ng, parity);
 }
 
 template <class S>
@@ -279,8 +287,9 @@ struct tpflbm_batch {
     int num_sms = 0;
     std::vector<tpflbm_t> inst;
     InstDesc* d_inst = nullptr;
-    BatchTmaInst* d_tinst = nullptr;  // TMA-staged variant: per-lattice maps and descriptors
-    int ntma = 0;                     // its TMA items (the first ntma of d_work[kTmaVariant])
+    BatchTmaInst* d_tinst = nullptr;  // TMA-staged variant: per-lattice maps and descriptors,
+    int4* d_titem = nullptr;          // its ntma TMA items (d_work[kTmaVariant] holds the rest)
+    int ntma = 0;
     int2* d_work[kNumVariants] = {};
     int nwork[kNumVariants] = {};
     int grid[kNumVariants] = {};
@@ -315,9 +324,9 @@ void launch_batch(tpflbm_batch_t b, int v, int parity)
     if (v == kTmaVariant) {
         const int ng = b->nwork[v] - b->ntma;
         if (b->storage == TPF_STORAGE_FP16)
-            launch_tma<StoreF16>(b->d_tinst, b->d_work[v], b->ntma, ng, parity, b->grid[v], b->stream);
+            launch_tma<StoreF16>(b->d_tinst, b->d_titem, b->ntma, b->d_work[v], ng, parity, b->grid[v], b->stream);
         else
-            launch_tma<StoreF32>(b->d_tinst, b->d_work[v], b->ntma, ng, parity, b->grid[v], b->stream);
+            launch_tma<StoreF32>(b->d_tinst, b->d_titem, b->ntma, b->d_work[v], ng, parity, b->grid[v], b->stream);
         return;
     }
     if (b->storage == TPF_STORAGE_FP16)
@@ -466,19 +475,34 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
             };
             interleave(edge);
             interleave(inner);
-            b->ntma = (int)work.size();
+            // TMA items also carry the tile's seam side (as seam_side) and whether it
+            // touches the lattice boundary (as the single-lattice kernel decides it)
+            std::vector<int4> titem(work.size());
+            for (size_t i = 0; i < work.size(); ++i) {
+                const int k = work[i].x, x0 = (work[i].y & 0xffff) * BX, y0 = (work[i].y >> 16) * BY;
+                const int seam = b->inst[k]->hp.bc_x != 0 ? 0 : (x0 == 0 ? -1 : (x0 + BX == nx[k] ? 1 : 0));
+                const bool eg = x0 <= 1 || x0 + BX >= nx[k] - 1 || y0 <= 1 || y0 + BY >= ny[k] - 1;
+                titem[i] = make_int4(k, work[i].y, seam, eg ? 1 : 0);
+            }
+            b->ntma = (int)titem.size();
+            work.clear();
             interleave(rest);
+            e = cudaMalloc(&b->d_titem, std::max<size_t>(1, titem.size()) * sizeof(int4));
+            if (e == cudaSuccess && !titem.empty())
+                e = cudaMemcpy(b->d_titem, titem.data(), titem.size() * sizeof(int4), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) break;
         } else {
             for (int k = 0; k < n; ++k)
                 for (int by = 0; by < ty[k]; ++by)
                     for (int bx = 0; bx < tx[k]; ++bx) work.push_back(make_int2(k, bx | (by << 16)));
         }
-        b->nwork[v] = (int)work.size();
+        b->nwork[v] = (int)work.size() + (v == kTmaVariant ? b->ntma : 0);
         if (b->storage == TPF_STORAGE_FP16) b->grid[v] = occupancy<StoreF16>(v) * b->num_sms;
         else b->grid[v] = occupancy<StoreF32>(v) * b->num_sms;
         b->grid[v] = std::min(b->grid[v], b->nwork[v]);
-        e = cudaMalloc(&b->d_work[v], work.size() * sizeof(int2));
-        if (e == cudaSuccess) e = cudaMemcpy(b->d_work[v], work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        e = cudaMalloc(&b->d_work[v], std::max<size_t>(1, work.size()) * sizeof(int2));
+        if (e == cudaSuccess && !work.empty())
+            e = cudaMemcpy(b->d_work[v], work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -645,6 +669,7 @@ void tpflbm_batch_destroy(tpflbm_batch_t b)
     for (int v = 0; v < kNumVariants; ++v) cudaFree(b->d_work[v]);
     cudaFree(b->d_inst);
     cudaFree(b->d_tinst);
+    cudaFree(b->d_titem);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -79,9 +79,10 @@ __device__ __forceinline__ int ref_source(const DevParams& P, int x, int y, int 
 }
 
 // ref_source for a node of a TMA tile: the writer's slot in the tile's record box
-// (origin x0 - 4, y0 - 2, RW x RH).  TMA tiles never need a periodic wrap.  Every
-// writer lies in the box; the clamps only keep the slot inside it when P itself is not
-// to be trusted (a batched tile whose copies, parameters included, timed out).
+// (origin x0 - 4, y0 - 2, RW x RH).  Records exist with FP16 storage only, whose TMA
+// tiles never need a periodic wrap.  Every writer lies in the box; the clamps only keep
+// the slot inside it when P itself is not to be trusted (a batched tile whose copies,
+// parameters included, timed out).
 __device__ __forceinline__ int ref_slot_box(const DevParams& P, int x, int y, int i, bool g_lbe, int x0, int y0,
                                             int RW, int RH)
 {
@@ -470,12 +471,40 @@ struct TmaLayout {
     static constexpr uint32_t TX_BYTES = 2 * F_BYTES + G_BYTES + U_BYTES + R_BYTES;
 };
 
+// Which side of a periodic x seam a TMA tile sits on: -1 its left ring column wraps to
+// x = nx - 1, +1 its right one to x = 0, 0 neither.  Seam tiles are staged by TMA with
+// FP32 storage only, and only in lattices at least two tiles wide (so no tile has both
+// sides); otherwise they take the general path and this is 0 for every TMA tile.  With
+// FP16 storage (records to patch as well) the seam code pushed the kernel to its
+// 128-register cap and slowed every tile (the 2048 x 512 channel, which has no seam,
+// by 3.5%).
+template <int BX>
+__device__ __forceinline__ int seam_side(const DevParams& P, int x0)
+{
+    if (P.bc_x != 0) return 0;
+    return x0 == 0 ? -1 : (x0 + BX == P.nx ? 1 : 0);
+}
+
 struct TmaMaps {
     CUtensorMap popF;  // populations, box FW x FH x 9 (used for f at z = 0 and h at z = 18)
     CUtensorMap popG;  // populations, box BX x BY x 9 (g at z = 9)
     CUtensorMap phiu;  // (phi u) planes, box BX x BY x 2
     CUtensorMap ref;   // FP16 reference records (8-byte elements), box RW x RH x 3
 };
+
+// The copies of one TMA tile into stage st, completing on bar (one elected thread).
+template <int BX, int BY, class S>
+__device__ __forceinline__ void tma_issue_tile(const TmaMaps& M, unsigned char* st, uint64_t* bar, int x0, int y0)
+{
+    using L = TmaLayout<BX, BY, S>;
+    fence_proxy_async();
+    mbar_expect_tx(bar, L::TX_BYTES);
+    tma_load_3d(st + L::OFF_F, &M.popF, bar, x0 - L::XP, y0 - 1, 0);
+    tma_load_3d(st + L::OFF_H, &M.popF, bar, x0 - L::XP, y0 - 1, 18);
+    tma_load_3d(st + L::OFF_G, &M.popG, bar, x0, y0, 9);
+    tma_load_3d(st + L::OFF_U, &M.phiu, bar, x0, y0, 0);
+    if constexpr (kRef<S>) tma_load_3d(st + L::OFF_R, &M.ref, bar, x0 - 4, y0 - 2, 0);
+}
 
 // phi, T and 1/(rho c_p) of a TMA tile and its ring
 template <int BX, int BY>
@@ -486,17 +515,46 @@ struct PhiSmem {
     float irc[SN];
 };
 
+// Periodic x seam (FP32 storage): the wrapped ring column of f and h from global memory
+// A into the box, where the copies left zeros, before anything decodes it (rows beyond
+// a wall stay zero: nothing decodes them).  Out of line: it runs for seam tiles only,
+// which wait one memory round trip here, and the stages keep their size.  Ends with a
+// block barrier.
+template <int BX, int BY, class S>
+__device__ __noinline__ void seam_patch(unsigned char* st, int seam, const typename S::elem* __restrict__ A, int nx,
+                                        int ny, long long pl, int y0)
+{
+    static_assert(!kRef<S>, "FP16 tiles are not staged across a seam");
+    using L = TmaLayout<BX, BY, S>;
+    using E = typename S::elem;
+    E* bF = (E*)(st + L::OFF_F);
+    E* bH = (E*)(st + L::OFF_H);
+    const int fc = seam < 0 ? L::XP - 1 : L::XP + BX, gx = seam < 0 ? nx - 1 : 0;
+    for (int k = threadIdx.x; k < 9 * L::FH; k += BX * BY) {
+        const int i = k / L::FH, y = y0 - 1 + k % L::FH;
+        if (y < 0 || y >= ny) continue;
+        const long long n = (long long)y * nx + gx;
+        bF[k * L::FW + fc] = A[i * pl + n];
+        bH[k * L::FW + fc] = A[(18 + i) * pl + n];
+    }
+    __syncthreads();
+}
+
 // The body of one TMA tile, shared by the single-lattice and the batched kernels: decode
 // the staged populations of the tile (stage st, landed unless ok is false) and its
 // ring, phi / T / 1/(rho c_p) into sm, one block barrier (which also votes on ok:
 // on_abort() runs on every thread and the tile returns true when any wait ran out),
 // after_ring() on every thread, then per node the macroscopic state, the collisions
 // and the push to B.  EDGE: the tile touches the lattice boundary (ghost ring nodes,
-// boundary records, boundary-aware push for every node).
+// boundary records, boundary-aware push for every node); seam (seam_side): the wrapped
+// column of a periodic x seam comes from A first.  EDGE and seam must be the
+// same on every thread and must not come from a staged P (it is not to be trusted
+// before the vote).
 template <int BX, int BY, class S, bool EDGE, class OnAbort, class AfterRing>
-__device__ __forceinline__ bool tma_tile(const DevParams& P, typename S::elem* __restrict__ B,
-                                         float* __restrict__ phiu, RefT* __restrict__ refB,
-                                         const unsigned char* st, PhiSmem<BX, BY>& sm, int x0, int y0, bool ok,
+__device__ __forceinline__ bool tma_tile(const DevParams& P, const typename S::elem* __restrict__ A,
+                                         typename S::elem* __restrict__ B, float* __restrict__ phiu,
+                                         RefT* __restrict__ refB,
+                                         unsigned char* st, PhiSmem<BX, BY>& sm, int x0, int y0, int seam, bool ok,
                                          OnAbort on_abort, AfterRing after_ring)
 {
     using L = TmaLayout<BX, BY, S>;
@@ -513,7 +571,28 @@ __device__ __forceinline__ bool tma_tile(const DevParams& P, typename S::elem* _
     const RefT* sR = (const RefT*)(st + L::OFF_R);
     (void)sR;
     constexpr bool edge = EDGE;
-    auto on_boundary = [&](int gx, int gy) { return gx == 0 || gx == P.nx - 1 || gy == 0 || gy == P.ny - 1; };
+    // nodes on a walled, inlet or outflow boundary (a periodic one has none), and ring
+    // nodes beyond one.  Only FP32 TMA tiles reach a periodic edge (x seams): the other
+    // TMA tiles keep one node clear of every periodic edge, where the plain tests agree.
+    constexpr bool kSeams = !kRef<S>;
+    auto on_boundary = [&](int gx, int gy) {
+        return ((!kSeams || P.bc_x != 0) && (gx == 0 || gx == P.nx - 1)) || gy == 0 || gy == P.ny - 1;
+    };
+    auto is_ghost = [&](int gx, int gy) {
+        return ((!kSeams || P.bc_x != 0) && (gx < 0 || gx >= P.nx)) || gy < 0 || gy >= P.ny;
+    };
+    if constexpr (edge) {
+        if constexpr (!kRef<S>) {
+            if (seam) {
+                // vote first: a batched tile's P and buffer pointers arrive with its copies
+                if (__syncthreads_or(!ok)) {
+                    on_abort();
+                    return true;
+                }
+                seam_patch<BX, BY, S>(st, seam, A, P.nx, P.ny, P.plane, y0);
+            }
+        }
+    }
 
     // decoded population i of ring slot (lx, ly) from the f (or h) box
     auto decF = [&](const E* box, float is, int rplane, int i, int lx, int ly, bool bnode) {
@@ -568,7 +647,7 @@ __device__ __forceinline__ bool tma_tile(const DevParams& P, typename S::elem* _
         else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
         const int k = ry * SX + rx;
         const int gx = x0 + rx - 1, gy = y0 + ry - 1;
-        const bool ghost = edge && (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny);
+        const bool ghost = edge && is_ghost(gx, gy);
         const bool rb = edge && on_boundary(gx, gy);
         float s = 0.f;
         if (ghost) {
@@ -596,7 +675,7 @@ __device__ __forceinline__ bool tma_tile(const DevParams& P, typename S::elem* _
             else if (r < 2 * SX + BY) { rx = 0; ry = r - 2 * SX + 1; }
             else { rx = BX + 1; ry = r - 2 * SX - BY + 1; }
             const int gx = x0 + rx - 1, gy = y0 + ry - 1;
-            const bool ox = gx < 0 || gx >= P.nx, oy = gy < 0 || gy >= P.ny;
+            const bool ox = (!kSeams || P.bc_x != 0) && (gx < 0 || gx >= P.nx), oy = gy < 0 || gy >= P.ny;
             if (ox || oy) {
                 const int mx = ox ? (gx < 0 ? 0 : P.nx - 1) : gx;
                 const int my = oy ? (gy < 0 ? 0 : P.ny - 1) : gy;
@@ -715,14 +794,7 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         int bx, by;
         tile_of(t, bx, by);
         const int x0 = bx * BX, y0 = by * BY;
-        unsigned char* st = dsm + s * L::STAGE;
-        fence_proxy_async();
-        mbar_expect_tx(&bar[s], L::TX_BYTES);
-        tma_load_3d(st + L::OFF_F, &maps.popF, &bar[s], x0 - L::XP, y0 - 1, 0);
-        tma_load_3d(st + L::OFF_H, &maps.popF, &bar[s], x0 - L::XP, y0 - 1, 18);
-        tma_load_3d(st + L::OFF_G, &maps.popG, &bar[s], x0, y0, 9);
-        tma_load_3d(st + L::OFF_U, &maps.phiu, &bar[s], x0, y0, 0);
-        if constexpr (kRef<S>) tma_load_3d(st + L::OFF_R, &maps.ref, &bar[s], x0 - 4, y0 - 2, 0);
+        tma_issue_tile<BX, BY, S>(maps, dsm + s * L::STAGE, &bar[s], x0, y0);
     };
 
     int it = 0;
@@ -757,10 +829,13 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
                 if (tn < ntma && tid == 0) issue(tn, s ^ 1);
             }
         };
-        const unsigned char* st = dsm + s * L::STAGE;
+        unsigned char* st = dsm + s * L::STAGE;
         const bool edge_tile = x0 <= 1 || x0 + BX >= P.nx - 1 || y0 <= 1 || y0 + BY >= P.ny - 1;
-        if (edge_tile ? tma_tile<BX, BY, S, true>(P, B, phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring)
-                      : tma_tile<BX, BY, S, false>(P, B, phiu, refB, st, sm, x0, y0, ok, on_abort, after_ring))
+        const int seam = seam_side<BX>(P, x0);
+        if (edge_tile ? tma_tile<BX, BY, S, true>(P, A, B, phiu, refB, st, sm, x0, y0, seam, ok, on_abort,
+                                                  after_ring)
+                      : tma_tile<BX, BY, S, false>(P, A, B, phiu, refB, st, sm, x0, y0, 0, ok, on_abort,
+                                                   after_ring))
             return;
         if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
     }

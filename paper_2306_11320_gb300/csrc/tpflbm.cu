@@ -545,11 +545,13 @@ void setup_tma(tpflbm_t h)
     const size_t e = sizeof(typename S::elem);
     h->tma = false;
     if (((size_t)nx * e) % 16 != 0 || ((size_t)nx * 4) % 16 != 0) return;
-    // TMA tiles: along a periodic axis the tile's (widened) halo inside the lattice;
-    // along a walled or inlet/outflow axis every whole tile (the copies fill the box
-    // beyond the lattice with zeros and the kernel applies the boundary rules there)
+    // TMA tiles: every whole tile along a walled or inlet/outflow axis (the copies fill
+    // the box beyond the lattice with zeros and the kernel applies the boundary rules
+    // there) and, with FP32 storage, along a periodic x axis at least two tiles wide (a
+    // seam tile fetches the wrapped columns from the other edge itself); otherwise, along
+    // a periodic axis, the tiles whose (widened) halo lies inside the lattice
     int bx_lo = 0, by_lo = 0, bx_hi = nx / kBX - 1, by_hi = ny / kBY - 1;
-    if (h->hp.bc_x == 0) {
+    if (h->hp.bc_x == 0 && (kRef<S> || nx < 2 * kBX)) {
         bx_lo = (L::XP + kBX - 1) / kBX;
         bx_hi = -1;  // last tile index with x0 + BX + XP <= nx
         for (int b = 0; (b + 1) * kBX + L::XP <= nx; ++b) bx_hi = b;
