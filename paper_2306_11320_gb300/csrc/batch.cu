@@ -31,8 +31,8 @@ struct InstDesc {
 // BY nodes, one thread per node) and, last, the TMA-staged path with 32 x 8 tiles.
 constexpr int kNumVariants = 5;
 constexpr int kTmaVariant = 4;
-constexpr int kVarBX[kNumVariants] = {32, 32, 32, 64, 32};
-constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4, 8};
+constexpr int kVarBX[kNumVariants] = {32, 32, 32, 64, kStepBX};
+constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4, kStepBY};
 
 // Persistent CTAs walk the work list of (instance, tile) pairs; each tile goes
 // through the general tile routine with its instance's parameters and buffers.
@@ -91,7 +91,9 @@ struct BatchTmaInst {  // aligned as its tensor maps
     BatchTileDesc d;
 };
 
-constexpr int kTBX = 32, kTBY = 8;  // tile of the TMA-staged batch kernel
+// tile of the TMA-staged batch kernel: the single-lattice step tile, in which each
+// lattice's TMA rectangle is laid out
+constexpr int kTBX = kStepBX, kTBY = kStepBY;
 
 template <class S>
 struct BatchLayout {

@@ -23,12 +23,7 @@ using namespace tpf;
 
 namespace {
 
-#ifndef TPF_TILE_BY
-#define TPF_TILE_BY 8
-#endif
-// step tile, one thread per node (measured on the 2048 x 512 channel: 32 x 16 tiles
-// run at 18.8 / 14.8 GLUPS against 21.3 / 16.7 for 32 x 8, FP32 / FP16)
-constexpr int kBX = 32, kBY = TPF_TILE_BY;
+constexpr int kBX = kStepBX, kBY = kStepBY;  // step tile (handle.h)
 constexpr int kMaxDevices = 64;
 constexpr long long kGraphSteps = 64;  // steps per replayed CUDA graph (even)
 
