@@ -224,6 +224,16 @@ int tpflbm_residual(tpflbm_t h, double dT, double out[3]);
 int tpflbm_project_phi(tpflbm_t h, const float *phi_pred, double target_sum, int mode, float *phi_out,
                        double *achieved);
 
+/* Self-check of the step kernels' bounded waits (their failure path, without a GPU
+ * fault): one block of 256 threads waits, with the same bounded wait the TMA-staged
+ * kernels use (at most `polls` polls here, about 2^22 there), on an mbarrier that
+ * nothing completes, then votes and raises a device flag as a step kernel raises its
+ * error flag.  *gave_up receives 1 when the wait ran out, the expected outcome, and 0
+ * otherwise.  No copy is ever in flight, so the context stays usable.  Runs on the
+ * default stream and synchronises it.  Errors: INVALID_ARG (polls < 1 or gave_up
+ * NULL), CUDA; the message is in tpflbm_last_error(NULL). */
+int tpflbm_check_bounded_wait(int polls, int *gave_up);
+
 /* Number of time steps taken since tpflbm_init. */
 long long tpflbm_time(tpflbm_t h);
 

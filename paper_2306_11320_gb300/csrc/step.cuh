@@ -446,11 +446,12 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// bounded wait: false after about 2^22 polls (each try_wait suspends for a while)
+// bounded wait: false after `limit` polls (about 2^22 in the step kernels; each
+// try_wait suspends for a while)
 constexpr uint32_t kWaitLimit = 1u << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit)
 {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -668,6 +668,25 @@ int stage_in(tpflbm_t h, const float* src, int k, float fill)
 
 // ------------------------------------------------------------------ C ABI
 
+namespace {
+
+// One block waits, with the step kernels' bounded wait, on an mbarrier that nothing
+// completes (no arrival, no copy in flight), then votes and raises the flag the way a
+// step kernel raises its error flag.
+__global__ void k_wait_check(uint32_t polls, int* flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, polls);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t tpflbm_workspace_bytes(int nx, int ny, const tpflbm_params* p)
@@ -1043,6 +1062,25 @@ int tpflbm_project_phi(tpflbm_t h, const float* phi_pred, double target_sum, int
     TPF_CUDA(h, cudaGetLastError());
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (achieved) *achieved = sums[0];
+    return TPF_OK;
+}
+
+int tpflbm_check_bounded_wait(int polls, int* gave_up)
+{
+    if (polls < 1 || !gave_up) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_check_bounded_wait: polls >= 1 and gave_up required");
+    *gave_up = 0;
+    int* flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_check<<<1, 256>>>((uint32_t)polls, flag);
+        e = cudaGetLastError();
+    }
+    int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tpflbm_check_bounded_wait");
+    *gave_up = v;
     return TPF_OK;
 }
 

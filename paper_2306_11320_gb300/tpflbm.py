@@ -77,6 +77,7 @@ SIGNATURES = {
     "tpflbm_batch_residual": ([_vp, _dp, _dp], _ip),
     "tpflbm_batch_variants": ([C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], _ip),
     "tpflbm_batch_set_variant": ([_vp, _ip], _ip),
+    "tpflbm_check_bounded_wait": ([C.c_int, C.POINTER(C.c_int)], _ip),
     "tpflbm_batch_tune": ([_vp, _ip, _dp, C.POINTER(C.c_int)], _ip),
     "tpflbm_batch_time": ([_vp], C.c_longlong),
     "tpflbm_batch_destroy": ([_vp], None),
@@ -102,6 +103,17 @@ def load_library(path: str | None = None, build: bool = True):
     if os.path.abspath(path) == os.path.abspath(LIB):
         _lib = lib
     return lib
+
+
+def check_bounded_wait(polls: int = 4096, lib=None) -> bool:
+    """tpflbm_check_bounded_wait: True when a bounded wait on an mbarrier that nothing
+    completes gave up after `polls` polls and raised its flag."""
+    lib = lib if lib is not None else load_library()
+    out = C.c_int(0)
+    rc = lib.tpflbm_check_bounded_wait(int(polls), C.byref(out))
+    if rc != 0:
+        raise TpfError(rc, lib.tpflbm_last_error(None).decode())
+    return bool(out.value)
 
 
 def make_params(p: dict, storage: int = STORAGE_FP32) -> Params:
