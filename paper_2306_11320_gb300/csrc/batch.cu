@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -90,6 +91,11 @@ struct BatchTmaInst {  // aligned as its tensor maps
     TmaMaps maps[2];      // by parity: the copies of a step at parity p read pop[p]
     BatchTileDesc d;
 };
+// the bulk copy wants 16-byte aligned addresses and a 16-byte multiple; the tensor maps
+// in the device array want 64-byte alignment
+static_assert(sizeof(BatchTileDesc) % 16 == 0, "bulk copy size");
+static_assert(offsetof(BatchTmaInst, d) % 16 == 0, "bulk copy source alignment");
+static_assert(alignof(BatchTmaInst) % 64 == 0 && sizeof(BatchTmaInst) % 64 == 0, "tensor map alignment");
 
 // tile of the TMA-staged batch kernel: the single-lattice step tile, in which each
 // lattice's TMA rectangle is laid out
