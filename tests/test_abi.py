@@ -75,3 +75,14 @@ def test_workspace_size_rejects_bad_sizes():
     assert lib.tpflbm_workspace_bytes(64, 64, C.byref(low)) == 0
     ok = make_params(WL.base_params(rho_l=0.5, cp_l=2.0))
     assert lib.tpflbm_workspace_bytes(64, 64, C.byref(ok)) > 0
+
+
+def test_bounded_wait_check_rejects_bad_arguments():
+    """tpflbm_check_bounded_wait validates its arguments before any CUDA call."""
+    from paper_2306_11320_gb300.tpflbm import load_library
+
+    lib = load_library()
+    out = C.c_int(7)
+    assert lib.tpflbm_check_bounded_wait(0, C.byref(out)) == -1  # TPF_ERR_INVALID_ARG
+    assert b"polls" in lib.tpflbm_last_error(None)
+    assert lib.tpflbm_check_bounded_wait(16, None) == -1
