@@ -443,8 +443,9 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
     for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
         std::vector<int2> work;
         const int BX = kVarBX[v], BY = kVarBY[v];
-        // tiles of all lattices, interleaved so that neighbouring items belong to
-        // different lattices (spreads each lattice's edge tiles over the CTAs)
+        // tiles of all lattices, lattice by lattice and row by row: the CTAs take
+        // consecutive items in the same round, so neighbouring tiles run together (their
+        // shared halo rows hit L2) and each lattice's edge tiles spread over the CTAs
         std::vector<int> tx(n), ty(n);
         long long total = 0;
         for (int k = 0; k < n; ++k) {
@@ -454,10 +455,11 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
         }
         work.reserve(total);
         if (v == kTmaVariant) {
-            // TMA items first: every lattice's boundary tiles, then its other tiles, each
-            // group interleaved over the lattices (at most one boundary tile per CTA while
-            // there are fewer of them than CTAs); then the general-path items
-            std::vector<std::vector<int2>> edge(n), inner(n), rest(n);
+            // TMA items first: every lattice's boundary tiles, interleaved over the lattices
+            // (at most one per CTA while there are fewer of them than CTAs), then the other
+            // TMA tiles lattice by lattice and row by row, as above; then the general-path
+            // items
+            std::vector<std::vector<int2>> edge(n), tma(n), rest(n);
             for (int k = 0; k < n; ++k) {
                 tpflbm_t h = b->inst[k];
                 for (int by = 0; by < ty[k]; ++by)
@@ -471,18 +473,18 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
                         }
                         const int x0 = bx * BX, y0 = by * BY;
                         const bool eg = x0 <= 1 || x0 + BX >= nx[k] - 1 || y0 <= 1 || y0 + BY >= ny[k] - 1;
-                        (eg ? edge[k] : inner[k]).push_back(it);
+                        (eg ? edge[k] : tma[k]).push_back(it);
                     }
             }
-            auto interleave = [&](std::vector<std::vector<int2>>& lists) {
-                size_t most = 0;
-                for (auto& l : lists) most = std::max(most, l.size());
-                for (size_t i = 0; i < most; ++i)
-                    for (auto& l : lists)
-                        if (i < l.size()) work.push_back(l[i]);
+            size_t most = 0;
+            for (auto& l : edge) most = std::max(most, l.size());
+            for (size_t i = 0; i < most; ++i)
+                for (auto& l : edge)
+                    if (i < l.size()) work.push_back(l[i]);
+            auto concat = [&](std::vector<std::vector<int2>>& lists) {
+                for (auto& l : lists) work.insert(work.end(), l.begin(), l.end());
             };
-            interleave(edge);
-            interleave(inner);
+            concat(tma);
             // TMA items also carry the tile's seam side (as seam_side) and whether it
             // touches the lattice boundary (as the single-lattice kernel decides it)
             std::vector<int4> titem(work.size());
@@ -494,7 +496,7 @@ int tpflbm_batch_create(int n, const int* nx, const int* ny, const tpflbm_params
             }
             b->ntma = (int)titem.size();
             work.clear();
-            interleave(rest);
+            concat(rest);
             e = cudaMalloc(&b->d_titem, std::max<size_t>(1, titem.size()) * sizeof(int4));
             if (e == cudaSuccess && !titem.empty())
                 e = cudaMemcpy(b->d_titem, titem.data(), titem.size() * sizeof(int4), cudaMemcpyHostToDevice);
