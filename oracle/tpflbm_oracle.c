@@ -18,8 +18,8 @@
  *   pass 4  pull streaming with the heat-capacitance weighted update of Eq. 28
  *           and the boundary rules of Sec. 4
  *
- * Readings of places where the paper is silent or garbled (all listed in the
- * design notes; the CUDA path takes the same readings):
+ * Readings of places where the paper is silent or garbled (the CUDA path takes
+ * the same readings):
  *   R1  D2Q9 weights 4/9, 1/9 (x4), 1/36 (x4) (the printed 4/9 for i=1..4 is a typo).
  *   R2  Isotropic central stencils: grad X = sum_i w_i c_i X(x+c_i) / cs2,
  *       lap X = sum_i 2 w_i (X(x+c_i) - X(x)) / cs2.  grad rho = d(rho)/d(phi) grad phi
