@@ -164,14 +164,14 @@ int tpflbm_set_state(tpflbm_t h, const float *f, const float *g, const float *hh
 int tpflbm_diagnostics(tpflbm_t h, double out[8]);
 
 /* Same eight reductions as tpflbm_diagnostics, for a state held in caller memory,
- * allocating no device memory at all.  (The paper has no counterpart: this serves
- * callers that cannot call cudaMalloc, such as code running inside a memory pool
- * or allocator callback, a CUDA graph being built from pre-planned buffers, or a
- * host that hands out only fixed buffers it owns.)
+ * allocating no device memory at all.  (The paper has no counterpart.  It serves
+ * callers that must not call cudaMalloc: code that runs inside a memory pool's or an
+ * allocator's own callback, where allocating would re-enter the allocator, and hosts
+ * that hand a library only fixed buffers they own and account for.)
  *   pop   device pointer, 27 population planes (f 0-8, g 9-17, h 18-26) of `plane`
  *         elements each, [ny][nx] inside a plane; float32, or float16 encoded as in
  *         tpflbm_params.storage when p->storage is TPF_STORAGE_FP16.
- *   plane elements per plane, >= nx * ny.
+ *   plane elements per plane, >= nx * ny (the buffers must hold 27, 3 and 2 planes).
  *   ref   FP16 storage only: the reference records of the previous step, three
  *         planes (f, g, h) of `plane` 8-byte records (float32 zeroth moment, then
  *         two halves, see tpflbm_params.storage); NULL for FP32.
@@ -179,18 +179,29 @@ int tpflbm_diagnostics(tpflbm_t h, double out[8]);
  *         previous step).
  *   out   8 doubles, host or device memory; same meaning as tpflbm_diagnostics.
  *   stream cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ * tpflbm_state_buffers gives these pointers for a handle's own state.
  * The kernel's scratch (per-block partial sums) is a fixed array of 1024 x 8 + 8
  * doubles (65,600 bytes) compiled into the library; every GPU that loads the
  * library holds it until the process exits.  Any lattice the library accepts
  * (nx, ny >= 3, nx * ny <= 2^30) fits, because the kernel walks the lattice with
  * at most 1024 blocks; larger sizes and invalid arguments return
- * TPF_ERR_INVALID_ARG (message in tpflbm_last_error(NULL)).  The first call on a
- * device looks up that array's device address, so make it before any stream
- * capture.  All calls share the array and each call overwrites every entry it
- * reads, so nothing needs clearing; calls whose work overlaps on the GPU (for
- * example on two streams) race on it and must be serialised by the caller. */
+ * TPF_ERR_INVALID_ARG (message in tpflbm_last_error(NULL)).  Each call looks up the
+ * array's address in the current context (cudaGetSymbolAddress, no allocation); on
+ * the first call on a device that lookup may also load the library's device code
+ * there, so make that first call before any stream capture.  All calls share the
+ * array and each call overwrites every entry it reads, so nothing needs clearing;
+ * calls whose work overlaps on the GPU (for example on two streams) race on it and
+ * must be serialised by the caller. */
 int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params *p, const void *pop, long long plane,
                               const void *ref, const float *phiu, double out[8], void *stream);
+
+/* Device pointers of the handle's current state (time tpflbm_time(h)), as
+ * tpflbm_diagnostics_static takes them: *pop the 27 population planes, *ref the three
+ * FP16 reference-record planes (NULL with FP32 storage), *phiu the two (phi u) planes,
+ * *plane the elements per plane (>= nx * ny, padded).  Any output pointer may be NULL.
+ * The pointers stay owned by the handle and change with every step (the two
+ * population buffers alternate); read them after the stream has finished the steps. */
+int tpflbm_state_buffers(tpflbm_t h, void **pop, void **ref, void **phiu, long long *plane);
 
 /* Steady-state residual (the paper states no convergence criterion; this is the one
  * the warm-start comparison uses).  With u, T the current fields and u', T' those of

@@ -9,7 +9,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -24,7 +23,6 @@ using namespace tpf;
 namespace {
 
 constexpr int kBX = kStepBX, kBY = kStepBY;  // step tile (handle.h)
-constexpr int kMaxDevices = 64;
 constexpr long long kGraphSteps = 64;  // steps per replayed CUDA graph (even)
 
 // ------------------------------------------------------- auxiliary kernels
@@ -935,29 +933,15 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void
     if (rc != TPF_OK) return fail(nullptr, rc, "tpflbm_diagnostics_static: " + why);
     if (!pop || !phiu || !out) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: pop, phiu and out are required");
     if (plane < (long long)nx * ny) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: plane must be >= nx * ny");
-    if (plane > (1LL << 31) / 27) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: plane too large");
     const bool f16 = p->storage == TPF_STORAGE_FP16;
     if (f16 && !ref) return fail(nullptr, TPF_ERR_INVALID_ARG, "tpflbm_diagnostics_static: FP16 storage needs the reference records");
 
-    // the scratch's device address on the current device, looked up once per device
-    static std::mutex mu;
-    static double* addr[kMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, TPF_ERR_UNSUPPORTED, "tpflbm_diagnostics_static: device index out of range");
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!addr[dev]) {
-            void* a = nullptr;
-            e = cudaGetSymbolAddress(&a, g_diag_scratch);
-            if (e != cudaSuccess)
-                return fail(nullptr, TPF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            addr[dev] = (double*)a;
-        }
-        scratch = addr[dev];
-    }
+    // the scratch's device address in the context current now (a lookup, no allocation;
+    // done on every call so that it follows the context after a reset or a switch)
+    void* a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_diag_scratch);
+    if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    double* scratch = (double*)a;
 
     DevParams P = make_dev_params(nx, ny, *p);
     P.plane = plane;
@@ -973,13 +957,33 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params* p, const void
     if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("k_reduce_partial: ") + cudaGetErrorString(e));
     double* res = scratch + kRedMaxBlocks * 8;
     k_reduce_final<<<1, 256, 0, s>>>(scratch, nb, res);
+    // one copy of the results on the caller's stream, then out from that host copy
+    double v[8];
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, 8 * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, res, sizeof(v), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaPointerAttributes at{};
+    if (e == cudaSuccess) e = cudaPointerGetAttributes(&at, out);
+    if (e == cudaSuccess) {
+        if (at.type == cudaMemoryTypeDevice) {
+            e = cudaMemcpyAsync(out, v, sizeof(v), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        } else {
+            std::memcpy(out, v, sizeof(v));
+        }
+    }
     if (e != cudaSuccess) return fail(nullptr, TPF_ERR_CUDA, std::string("tpflbm_diagnostics_static: ") + cudaGetErrorString(e));
-    double nf = 0.0;
-    if (cudaMemcpy(&nf, res + 7, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess && nf > 0)
-        return fail(nullptr, TPF_ERR_NONFINITE, "non-finite values in the state");
+    if (v[7] > 0) return fail(nullptr, TPF_ERR_NONFINITE, "non-finite values in the state");
+    return TPF_OK;
+}
+
+int tpflbm_state_buffers(tpflbm_t h, void** pop, void** ref, void** phiu, long long* plane)
+{
+    if (!h) return TPF_ERR_INVALID_ARG;
+    if (pop) *pop = h->pop[h->cur];
+    if (ref) *ref = h->dp.storage == TPF_STORAGE_FP16 ? (void*)h->ref[h->cur] : nullptr;
+    if (phiu) *phiu = h->phiu;
+    if (plane) *plane = h->dp.plane;
     return TPF_OK;
 }
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "tpflbm_set_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_diagnostics": ([_vp, _dp], _ip),
     "tpflbm_diagnostics_static": ([_ip, _ip, C.POINTER(Params), _vp, C.c_longlong, _vp, _vp, _vp, _vp], _ip),
+    "tpflbm_state_buffers": ([_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_longlong)], _ip),
     "tpflbm_residual": ([_vp, C.c_double, _dp], _ip),
     "tpflbm_project_phi": ([_vp, _vp, C.c_double, _ip, _vp, _dp], _ip),
     "tpflbm_time": ([_vp], C.c_longlong),
@@ -260,6 +261,14 @@ class Lattice:
         self._check(self.lib.tpflbm_project_phi(self.h, C.c_void_p(phi_pred.data_ptr()), float(target_sum), int(mode),
                                                 C.c_void_p(out.data_ptr()), C.byref(got)))
         return out, got.value
+
+    def state_buffers(self):
+        """tpflbm_state_buffers: (pop, ref, phiu, plane), device addresses of the current
+        state (ref is None with FP32 storage) and the elements per plane."""
+        pop, ref, phiu, plane = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_longlong()
+        self._check(self.lib.tpflbm_state_buffers(self.h, C.byref(pop), C.byref(ref), C.byref(phiu),
+                                                  C.byref(plane)))
+        return pop.value, ref.value, phiu.value, plane.value
 
     def diagnostics(self):
         out = (C.c_double * 8)()
