@@ -1,14 +1,19 @@
 """Benchmark of the fused coupled-LBM step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16] [--impl ours|reference]
+                [--flush] [--workload bubbles|ensemble|warmstart]
 
 One step = one pass of the whole hot path (moments, stencils, closures, forces,
 the three collisions, streaming and boundary rules) over the 2048 x 512 bubble
 channel (two bubbles, Poiseuille inlet, outflow, parabolic sigma(T)), with the
-state resident in HBM.  Each timed step is bracketed by CUDA events on the
-lattice's stream; an L2 flush (a 256 MiB write) runs between timed steps,
-outside the events.  Metric: lattice updates per second (MLUPS, one update = one
-node through all three LBEs), whole job.  Prints one JSON line.
+state resident in HBM.  The K timed steps run back to back between two CUDA events
+on the lattice's stream: each step reads one 113 MB population buffer and writes
+the other (plus 8 MB of (phi u)), 234 MB per step against the 126 MB L2, so a step
+finds at most the tail of the previous step's writes in L2 (ncu: DRAM reads per
+launch equal the algorithmic reads).  With --flush a 256 MiB write runs between
+timed steps instead, outside per-step events (that write leaves up to the whole L2
+dirty for the next step to write back).  Metric: lattice updates per second (MLUPS,
+one update = one node through all three LBEs), whole job.  Prints one JSON line.
 
 N > 1 (torchrun, one rank per GPU): independent replicas (the path has no
 data-path exchange); value = all ranks' updates / max-over-ranks time.
@@ -206,7 +211,7 @@ def bench_ours(args, rank, world, local_rank):
     lat = Lattice(NX, NY, params, storage=storage, stream=stream)
     f32 = {k: v.astype(np.float32) for k, v in fields.items()}
     lat.init(**f32)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev) if args.flush else None
 
     def barrier():
         if world > 1:
@@ -216,30 +221,46 @@ def bench_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             lat.step(1)
-            flush.fill_(1)
-        barrier()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        with ClockSampler(local_rank) as clk:
-            for k in range(args.steps):
-                starts[k].record(stream)
-                lat.step(1)
-                ends[k].record(stream)
+            if args.flush:
                 flush.fill_(1)
-            barrier()
-        times = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    total_ms = max_over_ranks(sum(times), world, dev)
+        barrier()
+        with ClockSampler(local_rank) as clk:
+            if args.flush:
+                starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+                ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+                for k in range(args.steps):
+                    starts[k].record(stream)
+                    lat.step(1)
+                    ends[k].record(stream)
+                    flush.fill_(1)
+                barrier()
+                times = [a.elapsed_time(b) for a, b in zip(starts, ends)]  # ms
+                step_ms = sum(times)
+            else:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    lat.step(1)
+                e1.record(stream)
+                barrier()
+                step_ms = e0.elapsed_time(e1)
+    total_ms = max_over_ranks(step_ms, world, dev)
     diag = lat.diagnostics()
 
-    # end to end through the public API with host buffers: H2D of the initial fields,
-    # K steps, D2H of the final fields, all inside the timed region
+    # end to end through the public API with host buffers: H2D of the initial fields
+    # from pinned memory, then every step the step itself and a D2H read of its FP64
+    # diagnostics (sum phi, sum rho c_p T, ..., 64 B), and D2H of the final fields
     host_in = {k: torch.from_numpy(v).pin_memory() for k, v in f32.items()}
     host_out = [torch.empty((NY, NX), dtype=torch.float32).pin_memory() for _ in range(5)]
+    import ctypes
+    dbuf = (ctypes.c_double * 8)()
     barrier()
     t0 = time.perf_counter()
     lat.init(**host_in)
-    lat.step(args.steps)
-    lat._check(lat.lib.tpflbm_get_fields(lat.h, *[__import__("ctypes").c_void_p(t.data_ptr()) for t in host_out]))
+    for _ in range(args.steps):
+        lat._check(lat.lib.tpflbm_step(lat.h, 1))
+        lat._check(lat.lib.tpflbm_diagnostics(lat.h, dbuf))
+    lat._check(lat.lib.tpflbm_get_fields(lat.h, *[ctypes.c_void_p(t.data_ptr()) for t in host_out]))
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
 
@@ -263,7 +284,9 @@ def bench_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "storage": args.storage, "normal": args.normal, "collision": args.collision,
-                   "l2": "256 MiB L2 flush between timed steps", "parallelism": "replicas"},
+                   "l2": ("256 MiB L2 flush between timed steps" if args.flush else
+                          "inputs > L2: 234 MB read+written per step vs 126 MB L2, steps back to back"),
+                   "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(args.storage),
                      "peak_source": peak_kind, "alg_bytes_per_launch": alg,
@@ -271,7 +294,7 @@ def bench_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": {"value": units / e2e_s / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": field_bytes / args.steps,
-                "d2h_bytes_per_step": field_bytes / args.steps},
+                "d2h_bytes_per_step": field_bytes / args.steps + 64},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "check": {"nonfinite": diag["nonfinite"], "sum_phi": diag["sum_phi"]},
@@ -389,6 +412,8 @@ def main():
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--flush", action="store_true",
+                    help="write 256 MiB between timed steps (per-step events) instead of timing steps back to back")
     ap.add_argument("--workload", choices=("bubbles", "ensemble", "warmstart"), default="bubbles",
                     help="bubbles: the 2048x512 channel (the headline line); ensemble: the "
                          "256-lattice parameter sweep through the batched launch; warmstart: time to "

@@ -203,6 +203,22 @@ int tpflbm_diagnostics_static(int nx, int ny, const tpflbm_params *p, const void
  * population buffers alternate); read them after the stream has finished the steps. */
 int tpflbm_state_buffers(tpflbm_t h, void **pop, void **ref, void **phiu, long long *plane);
 
+/* Per-bubble migration velocity and position of Sec. 4.3 (the paper's u_b,alpha and
+ * x_b,alpha, after Eq. 63): the bubbles are the connected regions of phi < 0 of the
+ * current state (4-neighbour connectivity, wrapping along periodic axes), labelled on
+ * the device; for each, FP64 sums over its nodes give
+ *   out[6k + 0] number of nodes,      out[6k + 1] sum phi (negative),
+ *   out[6k + 2] u_b = sum phi u_x / sum phi,   out[6k + 3] v_b = sum phi u_y / sum phi,
+ *   out[6k + 4] x_b = sum phi x / sum phi,     out[6k + 5] y_b = sum phi y / sum phi,
+ * with (x, y) node coordinates (node (x, y) at x, y; along a periodic axis each node is
+ * taken at its image nearest to the region's first node, so a bubble that straddles the
+ * seam keeps one centroid, reported in [0, nx) or [0, ny)).  Bubbles are ordered by x_b
+ * (then y_b); *count receives their number and the first min(*count, max_bubbles) are
+ * written to out (6 doubles each; out may be NULL when max_bubbles is 0).  At most 32
+ * separate regions are supported (TPF_ERR_UNSUPPORTED beyond).  Uses the lattice's
+ * staging and reduction memory (not its state) and synchronises its stream. */
+int tpflbm_bubbles(tpflbm_t h, int max_bubbles, double *out, int *count);
+
 /* Steady-state residual (the paper states no convergence criterion; this is the one
  * the warm-start comparison uses).  With u, T the current fields and u', T' those of
  * the previous call, K steps earlier, and N = nx * ny:

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -359,6 +360,107 @@ __global__ void k_project_apply(const float* __restrict__ a, long long N, double
 {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
         out[n] = (float)tanh((double)a[n] + s);
+}
+
+// Bubbles of Sec. 4.3: the connected regions of phi < 0 (4-connectivity, wrapping
+// along periodic axes), each with its FP64 moments.  Labels are node indices: every
+// node of the set starts with its own index and repeatedly takes the smallest label
+// among itself, its in-set neighbours and its label's label (pointer jumping).  Labels
+// only decrease and always name a node of the same region, so the fixed point gives
+// every node of a region the region's smallest node index, its root.
+constexpr int kMaxBubbles = 32;
+constexpr int kBubBlocks = 40;  // kBubBlocks x kMaxBubbles x 6 partials + results fit the reduction area
+static_assert((kBubBlocks + 1) * kMaxBubbles * 6 <= kRedMaxBlocks * 8 + 8, "bubble sums fit the reduction area");
+
+__global__ void k_lab_init(const float* __restrict__ phi, long long N, int* __restrict__ lab)
+{
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
+        lab[n] = phi[n] < 0.f ? (int)n : -1;
+}
+
+__global__ void k_lab_hook(int nx, int ny, int bc_x, int bc_y, int* lab, int* changed)
+{
+    const long long N = (long long)nx * ny;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int l = lab[n];
+        if (l < 0) continue;
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        int m = min(l, lab[l]);
+        const int nb[4][2] = {{x + 1, y}, {x - 1, y}, {x, y + 1}, {x, y - 1}};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int qx = nb[k][0], qy = nb[k][1];
+            if (bc_x == 0) qx = wrap(qx, nx);
+            if (bc_y == 1) qy = wrap(qy, ny);
+            if (qx < 0 || qx >= nx || qy < 0 || qy >= ny) continue;
+            const int lq = lab[(long long)qy * nx + qx];
+            if (lq >= 0 && lq < m) m = lq;
+        }
+        if (m < l) {
+            atomicMin(&lab[n], m);
+            atomicMin(&lab[l], m);  // the old label's node joins too (same region)
+            *changed = 1;
+        }
+    }
+}
+
+__global__ void k_lab_roots(const int* __restrict__ lab, long long N, int* __restrict__ count, int* __restrict__ roots)
+{
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
+        if (lab[n] == (int)n) {
+            const int k = atomicAdd(count, 1);
+            if (k < kMaxBubbles) roots[k] = (int)n;
+        }
+}
+
+struct RootList {
+    int n;
+    int r[kMaxBubbles];
+};
+
+// Per block and bubble: node count, sum phi, sum phi u_x, sum phi u_y, sum phi dx,
+// sum phi dy, with (dx, dy) the node's offset from its root, taken to the nearest
+// periodic image along periodic axes.
+__global__ void __launch_bounds__(256)
+k_bubble_partial(int nx, int ny, int bc_x, int bc_y, const float* __restrict__ phi, const float* __restrict__ ux,
+                 const float* __restrict__ uy, const int* __restrict__ lab, const RootList roots,
+                 double* __restrict__ partial)
+{
+    __shared__ double acc[kMaxBubbles][6];
+    for (int k = threadIdx.x; k < kMaxBubbles * 6; k += blockDim.x) acc[k / 6][k % 6] = 0.0;
+    __syncthreads();
+    const long long N = (long long)nx * ny;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const int l = lab[n];
+        if (l < 0) continue;
+        int b = -1;
+        for (int k = 0; k < roots.n; ++k)
+            if (roots.r[k] == l) b = k;
+        if (b < 0) continue;
+        int dx = (int)(n % nx) - l % nx, dy = (int)(n / nx) - l / nx;
+        if (bc_x == 0) dx = dx > nx / 2 ? dx - nx : (dx < -nx / 2 ? dx + nx : dx);
+        if (bc_y == 1) dy = dy > ny / 2 ? dy - ny : (dy < -ny / 2 ? dy + ny : dy);
+        const double ph = phi[n];
+        atomicAdd(&acc[b][0], 1.0);
+        atomicAdd(&acc[b][1], ph);
+        atomicAdd(&acc[b][2], ph * ux[n]);
+        atomicAdd(&acc[b][3], ph * uy[n]);
+        atomicAdd(&acc[b][4], ph * dx);
+        atomicAdd(&acc[b][5], ph * dy);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < roots.n * 6; k += blockDim.x)
+        partial[(blockIdx.x * kMaxBubbles + k / 6) * 6 + k % 6] = acc[k / 6][k % 6];
+}
+
+// sums of the block partials in block order (one thread per bubble and quantity)
+__global__ void k_bubble_final(const double* __restrict__ partial, int nblocks, int nb, double* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb * 6) return;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += partial[(b * kMaxBubbles + k / 6) * 6 + k % 6];
+    out[k] = v;
 }
 
 }  // namespace
@@ -1066,6 +1168,86 @@ int tpflbm_project_phi(tpflbm_t h, const float* phi_pred, double target_sum, int
     TPF_CUDA(h, cudaGetLastError());
     TPF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (achieved) *achieved = sums[0];
+    return TPF_OK;
+}
+
+int tpflbm_bubbles(tpflbm_t h, int max_bubbles, double* out, int* count)
+{
+    if (!h || max_bubbles < 0 || (max_bubbles > 0 && !out) || !count)
+        return fail(h, TPF_ERR_INVALID_ARG, "tpflbm_bubbles needs count, and out when max_bubbles > 0");
+    int rc = check_err(h);
+    if (rc) return rc;
+    const long long N = (long long)h->nx * h->ny;
+    const long long pl = h->dp.plane;
+    const int c = h->cur;
+    // phi, u_x, u_y of the current state into staging planes 0-2 (as tpflbm_get_fields)
+    if (h->dp.storage == TPF_STORAGE_FP16)
+        k_fields<StoreF16><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const __half*)h->pop[c], h->ref[c], h->phiu, h->stage);
+    else
+        k_fields<StoreF32><<<grid_1d(N), 256, 0, h->stream>>>(h->dp, (const float*)h->pop[c], h->ref[c], h->phiu, h->stage);
+    TPF_CUDA(h, cudaGetLastError());
+    int* lab = (int*)(h->stage + 5 * pl);
+    int* roots = (int*)(h->stage + 6 * pl);  // kMaxBubbles entries
+    int* flags = h->err + 1;                   // [0] changed, [1] root count
+    k_lab_init<<<grid_1d(N), 256, 0, h->stream>>>(h->stage, N, lab);
+    TPF_CUDA(h, cudaGetLastError());
+    // propagate to the fixed point, checking for changes every 4 sweeps; a region of
+    // n nodes settles within n sweeps (pointer jumping makes it far fewer)
+    const long long max_sweeps = N + 8;
+    long long sweeps = 0;
+    for (;;) {
+        int changed = 0;
+        TPF_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(int), h->stream));
+        for (int k = 0; k < 4; ++k)
+            k_lab_hook<<<grid_1d(N), 256, 0, h->stream>>>(h->nx, h->ny, h->dp.bc_x, h->dp.bc_y, lab, flags);
+        TPF_CUDA(h, cudaGetLastError());
+        TPF_CUDA(h, cudaMemcpyAsync(&changed, flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+        sweeps += 4;
+        if (!changed) break;
+        if (sweeps > max_sweeps) return fail(h, TPF_ERR_UNSUPPORTED, "tpflbm_bubbles: labelling did not settle");
+    }
+    TPF_CUDA(h, cudaMemsetAsync(flags + 1, 0, sizeof(int), h->stream));
+    k_lab_roots<<<grid_1d(N), 256, 0, h->stream>>>(lab, N, flags + 1, roots);
+    TPF_CUDA(h, cudaGetLastError());
+    RootList rl{};
+    int nroots = 0;
+    TPF_CUDA(h, cudaMemcpyAsync(&nroots, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    TPF_CUDA(h, cudaMemcpyAsync(rl.r, roots, sizeof(rl.r), cudaMemcpyDeviceToHost, h->stream));
+    TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (nroots > kMaxBubbles)
+        return fail(h, TPF_ERR_UNSUPPORTED, "tpflbm_bubbles: more than 32 separate regions of phi < 0");
+    rl.n = nroots;
+    std::sort(rl.r, rl.r + nroots);
+    *count = nroots;
+    if (nroots == 0 || max_bubbles == 0) return TPF_OK;
+    double* part = h->red;
+    double* res = h->red + kBubBlocks * kMaxBubbles * 6;
+    k_bubble_partial<<<kBubBlocks, 256, 0, h->stream>>>(h->nx, h->ny, h->dp.bc_x, h->dp.bc_y, h->stage, h->stage + pl,
+                                                        h->stage + 2 * pl, lab, rl, part);
+    TPF_CUDA(h, cudaGetLastError());
+    k_bubble_final<<<1, kMaxBubbles * 6, 0, h->stream>>>(part, kBubBlocks, nroots, res);
+    TPF_CUDA(h, cudaGetLastError());
+    double sums[kMaxBubbles * 6];
+    TPF_CUDA(h, cudaMemcpyAsync(sums, res, nroots * 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TPF_CUDA(h, cudaStreamSynchronize(h->stream));
+    // per bubble: nodes, sum phi, u_b, v_b, x_b, y_b; ordered by x_b, then y_b
+    double rows[kMaxBubbles][6];
+    for (int k = 0; k < nroots; ++k) {
+        const double* v = sums + 6 * k;
+        const int xr = rl.r[k] % h->nx, yr = rl.r[k] / h->nx;
+        double xb = xr + v[4] / v[1], yb = yr + v[5] / v[1];
+        if (h->dp.bc_x == 0) xb = std::fmod(xb + h->nx, (double)h->nx);
+        if (h->dp.bc_y == 1) yb = std::fmod(yb + h->ny, (double)h->ny);
+        const double r[6] = {v[0], v[1], v[2] / v[1], v[3] / v[1], xb, yb};
+        std::memcpy(rows[k], r, sizeof(r));
+    }
+    int order[kMaxBubbles];
+    for (int k = 0; k < nroots; ++k) order[k] = k;
+    std::sort(order, order + nroots, [&](int a, int b) {
+        return rows[a][4] < rows[b][4] || (rows[a][4] == rows[b][4] && rows[a][5] < rows[b][5]);
+    });
+    for (int k = 0; k < nroots && k < max_bubbles; ++k) std::memcpy(out + 6 * k, rows[order[k]], 6 * sizeof(double));
     return TPF_OK;
 }
 

@@ -62,6 +62,7 @@ SIGNATURES = {
     "tpflbm_diagnostics": ([_vp, _dp], _ip),
     "tpflbm_diagnostics_static": ([_ip, _ip, C.POINTER(Params), _vp, C.c_longlong, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_state_buffers": ([_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(C.c_longlong)], _ip),
+    "tpflbm_bubbles": ([_vp, _ip, _dp, C.POINTER(C.c_int)], _ip),
     "tpflbm_residual": ([_vp, C.c_double, _dp], _ip),
     "tpflbm_project_phi": ([_vp, _vp, C.c_double, _ip, _vp, _dp], _ip),
     "tpflbm_time": ([_vp], C.c_longlong),
@@ -269,6 +270,17 @@ class Lattice:
         self._check(self.lib.tpflbm_state_buffers(self.h, C.byref(pop), C.byref(ref), C.byref(phiu),
                                                   C.byref(plane)))
         return pop.value, ref.value, phiu.value, plane.value
+
+    BUBBLE_KEYS = ("nodes", "sum_phi", "u_b", "v_b", "x_b", "y_b")
+
+    def bubbles(self, max_bubbles: int = 32):
+        """tpflbm_bubbles: the connected phi < 0 regions of the current state (Sec. 4.3),
+        ordered by x_b, as a list of dicts with BUBBLE_KEYS."""
+        out = (C.c_double * (6 * max_bubbles))()
+        n = C.c_int()
+        self._check(self.lib.tpflbm_bubbles(self.h, int(max_bubbles), out, C.byref(n)))
+        vals = np.array(out[:]).reshape(max_bubbles, 6)
+        return [dict(zip(self.BUBBLE_KEYS, row)) for row in vals[:min(n.value, max_bubbles)]]
 
     def diagnostics(self):
         out = (C.c_double * 8)()

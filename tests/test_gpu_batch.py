@@ -65,9 +65,9 @@ def test_batch_matches_single_lattices(variant):
 
 def test_batch_matches_oracle():
     """Against the FP64 oracle once the flows have developed (a few steps from rest
-    the velocities are ~1e-9 and their relative error is pure rounding noise).  Two
-    float32 evaluations in different operation order differ by a random factor, so
-    the bound is 10x the float32 oracle's own deviation (or 1e-5)."""
+    the velocities are ~1e-9 and their relative error is pure rounding noise): each
+    field within max(1e-5, 3 x the float32 oracle's own deviation), the single-lattice
+    bound."""
     members = _members()
     b = _batch(members)
     steps = 300
@@ -82,7 +82,7 @@ def test_batch_matches_oracle():
         o32.step(steps)
         a, ref, fl = b.fields(k), o.fields(), o32.fields()
         for n in FIELDS:
-            bound = max(1e-5, 10.0 * rel_l2(fl[n], ref[n]))
+            bound = max(1e-5, 3.0 * rel_l2(fl[n], ref[n]))
             assert rel_l2(a[n], ref[n]) <= bound, (k, n, rel_l2(a[n], ref[n]), bound)
     d, rc = b.diagnostics()
     assert rc == 0 and d.shape == (len(members), 8) and np.all(d[:, 7] == 0)

@@ -19,7 +19,7 @@ from paper_2306_11320_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("phi", "ux", "uy", "p", "T")
+from fieldcheck import FIELDS, rel_l2  # noqa: E402
 
 
 def _lattice(nx, ny, params, **kw):
@@ -28,22 +28,10 @@ def _lattice(nx, ny, params, **kw):
     return Lattice(nx, ny, params, **kw)
 
 
-def rel_l2(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    den = np.sqrt((b ** 2).sum())
-    return float(np.sqrt(((a - b) ** 2).sum()) / den) if den > 0 else float(np.abs(a - b).max())
-
-
 def _check_fields(a, b, tol, floor=None):
-    """a: GPU fields, b: FP64 oracle fields, floor: float32-oracle fields or None."""
-    errs = {k: rel_l2(a[k], b[k]) for k in FIELDS}
-    bound = {k: tol for k in FIELDS}
-    if floor is not None:
-        bound = {k: max(tol, 3.0 * rel_l2(floor[k], b[k])) for k in FIELDS}
-    bad = {k: (errs[k], bound[k]) for k in FIELDS if not errs[k] <= bound[k]}
-    assert not bad, bad
-    return errs
+    from fieldcheck import check_fields
+
+    return {k: v[0] for k, v in check_fields(a, b, tol, floor).items()}
 
 
 def _pair(nx, ny, params, fields, floor=False, **kw):
@@ -146,38 +134,6 @@ def test_bubbles_full_size():
     gpu, orc, o32 = _pair(2048, 512, p, f, floor=True)
     _run_all((gpu, orc, o32), 20)
     _check_fields(gpu.fields(), orc.fields(), 1e-5, o32.fields())
-
-
-@pytest.fixture(scope="module")
-def bubbles_1000():
-    """The 2048 x 512 two-bubble channel after 1000 steps in the FP64 and float32
-    oracles (about half a minute each on the host cores)."""
-    p, f, _ = WL.bubbles()
-    f32 = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in f.items()}
-    o = OracleSim(2048, 512, p)
-    o.init(**f32)
-    o.step(1000)
-    o32 = OracleSim(2048, 512, p, real="float")
-    o32.init(**f32)
-    o32.step(1000)
-    return p, f, o.fields(), o32.fields()
-
-
-@pytest.mark.parametrize("storage", [0, 1])
-def test_bubbles_full_size_1000_steps(bubbles_1000, storage):
-    """The bench workload at its full size through the TMA kernel the bench times:
-    every field after 1000 steps within max(1e-5, 3 x the float32 floor) (FP32) or
-    5e-3 (FP16) of the FP64 oracle, compared on every node."""
-    p, f, ref, fl = bubbles_1000
-    if storage:
-        p = dict(p, **WL.fp16_scales(p))
-    lat = _lattice(2048, 512, p, storage=storage)
-    lat.init(**{k: np.asarray(v, dtype=np.float32) for k, v in f.items()})
-    lat.step(1000)
-    if storage:
-        _check_fields(lat.fields(), ref, 5e-3)
-    else:
-        _check_fields(lat.fields(), ref, 1e-5, fl)
 
 
 @pytest.mark.parametrize("case", ["random", "drop"])
@@ -317,9 +273,12 @@ def test_fp16_two_step_populations(nx, ny, bc_x, bc_y, law):
     gpu.step(2)
     orc.step(2)
     a, b = gpu.get_state(), orc.get_state()
-    # (phi u) is float32 but formed from decoded populations, so it carries the codec's
-    # error through phi and u: it gets the looser 2^-6
-    for k, tol in (("f", 2.0 ** -10), ("g", 2.0 ** -8), ("h", 2.0 ** -10), ("phiu", 2.0 ** -6)):
+    # (phi u) is float32 but formed from decoded populations: phi = sum f_i and
+    # rho u = sum c_i g_i + F/2 each add up to eight decoded populations, so (phi u)
+    # inherits a few times the population bound of g (2^-8 of g's largest population,
+    # which is of the order of the largest momentum here): 2^-9 of its own scale
+    # (measured 2.2e-4); a decode against a wrong record is off by ~1e-2
+    for k, tol in (("f", 2.0 ** -10), ("g", 2.0 ** -8), ("h", 2.0 ** -10), ("phiu", 2.0 ** -9)):
         scale = np.abs(b[k]).max()
         err = np.abs(a[k] - b[k]).max()
         assert err <= tol * scale, (k, err, scale)
