@@ -141,6 +141,12 @@ int tpflbm_init_forced(tpflbm_t h, const float *phi, const float *ux, const floa
  * on the handle's stream; returns after enqueueing. */
 int tpflbm_step(tpflbm_t h, long long nsteps);
 
+/* Wait for the steps enqueued so far and report whether they completed: TPF_OK, or
+ * TPF_ERR_TIMEOUT when a step kernel gave up waiting for its shared-memory copies (a
+ * 4-byte device flag read back on the handle's stream), or TPF_ERR_CUDA.  Synchronises
+ * the stream. */
+int tpflbm_status(tpflbm_t h);
+
 /* Macroscopic fields of the current state, as the next step computes them:
  * phi = sum f_i, T = sum h_i, u from rho u = sum c_i g_i + (Fs + G)/2 and p from the
  * pressure moment of Sec. 3.1.  Each output is a caller-owned [ny][nx] float32

@@ -43,6 +43,7 @@ struct tpflbm {
     bool tma = false;
     tpf::TmaMaps maps[2]{};             // maps[c]: reading pop[c]
     int bx0 = 0, by0 = 0, ntbx = 0, ntby = 0, grid_tma = 0;
+    int2* tiles = nullptr;              // (x0, y0) of the TMA tiles in the order the kernel walks them
     // CUDA graphs of kGraphSteps steps starting from pop[0] / pop[1] (captured on first use)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long t = 0;

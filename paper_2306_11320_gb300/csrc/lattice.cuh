@@ -92,6 +92,24 @@ struct Macro {
     float Fx, Fy, grx, gry, dpux, dpuy, nx, ny, Fhat;
 };
 
+// D2Q9 sums written out term by term.  A loop over i with coefficients c_ix, c_iy
+// would multiply by zero for the directions without that component, which IEEE
+// arithmetic does not let the compiler drop.
+//   first moment: (sum_i c_ix q_i, sum_i c_iy q_i)
+__device__ __forceinline__ void dq9_moment1(const float* q, float& mx, float& my)
+{
+    const float a = q[5] - q[7], b = q[8] - q[6];  // c_5 = (1,1) vs c_7, c_8 = (1,-1) vs c_6
+    mx = (q[1] - q[3]) + (a + b);
+    my = (q[2] - q[4]) + (a - b);
+}
+//   isotropic gradient: sum_i w_i c_i X_i / cs2 = (X_1 - X_3)/3 + (X_5 - X_7 + X_8 - X_6)/12, ...
+__device__ __forceinline__ void dq9_grad(const float* X, float& gx, float& gy)
+{
+    const float a = X[5] - X[7], b = X[8] - X[6];
+    gx = fmaf(1.f / 3.f, X[1] - X[3], (1.f / 12.f) * (a + b));
+    gy = fmaf(1.f / 3.f, X[2] - X[4], (1.f / 12.f) * (a - b));
+}
+
 // Per-node macroscopic state of one time level.  phin[i] and Tn[i] are phi and T at
 // x + c_i (ghost values outside the fluid already applied), phin[0] = phi(x).
 __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, const float* g,
@@ -103,16 +121,12 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     m.phi = phi;
     m.T = T;
     // isotropic stencils: grad X = sum w_i c_i X_i / cs2, lap X = sum 2 w_i (X_i - X_0) / cs2
-    float gpx = 0.f, gpy = 0.f, lap = 0.f, gtx = 0.f, gty = 0.f;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        gpx += wq(i) * cx(i) * phin[i];
-        gpy += wq(i) * cy(i) * phin[i];
-        lap += wq(i) * (phin[i] - phi);
-        gtx += wq(i) * cx(i) * Tn[i];
-        gty += wq(i) * cy(i) * Tn[i];
-    }
-    gpx *= kInvCs2; gpy *= kInvCs2; lap *= 2.f * kInvCs2; gtx *= kInvCs2; gty *= kInvCs2;
+    float gpx, gpy, gtx, gty;
+    dq9_grad(phin, gpx, gpy);
+    dq9_grad(Tn, gtx, gty);
+    const float lap_axis = ((phin[1] - phi) + (phin[3] - phi)) + ((phin[2] - phi) + (phin[4] - phi));
+    const float lap_diag = ((phin[5] - phi) + (phin[7] - phi)) + ((phin[6] - phi) + (phin[8] - phi));
+    const float lap = fmaf(2.f / 3.f, lap_axis, (1.f / 6.f) * lap_diag);
 
     // closures, Eq. 45
     const float pc = clamp1(phi);
@@ -153,13 +167,9 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     m.Fy = Fy;
 
     // velocity and pressure moments of the NS populations
-    float mx = 0.f, my = 0.f, sne0 = 0.f;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        mx += cx(i) * g[i];
-        my += cy(i) * g[i];
-        sne0 += g[i];
-    }
+    float mx, my;
+    dq9_moment1(g, mx, my);
+    const float sne0 = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
     const float ux = (mx + 0.5f * Fx) * inv_rho;
     const float uy = (my + 0.5f * Fy) * inv_rho;
     const float grx = P.drho_dphi * gpx, gry = P.drho_dphi * gpy;
@@ -180,14 +190,10 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     if (P.normal_law == 1) {
         // local recovery (Sec. 3): J = sum_i c_i (f_i - f_i^eq) + d_t(phi u)/2 =
         // -cs2 tau_phi grad phi + M_phi Theta n, so n = -J/|J|; sum_i c_i f_i^eq = phi u
-        float jx = 0.5f * m.dpux - phi * ux, jy = 0.5f * m.dpuy - phi * uy;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            if (cx(i) != 0) jx += (float)cx(i) * f[i];
-            if (cy(i) != 0) jy += (float)cy(i) * f[i];
-        }
-        nvx = -jx;
-        nvy = -jy;
+        float jx, jy;
+        dq9_moment1(f, jx, jy);
+        nvx = -(jx + 0.5f * m.dpux - phi * ux);
+        nvy = -(jy + 0.5f * m.dpuy - phi * uy);
         nthr = P.jthr2;
     }
     const float gn2 = nvx * nvx + nvy * nvy;
@@ -201,12 +207,8 @@ __device__ __forceinline__ Macro node_macro(const DevParams& P, const float* f, 
     }
 
     // local grad T from the non-equilibrium part of h (Eq. 40), thermal source of Eq. 27
-    float qx = 0.f, qy = 0.f;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        qx += cx(i) * h[i];
-        qy += cy(i) * h[i];
-    }
+    float qx, qy;
+    dq9_moment1(h, qx, qy);
     const float k = -m.inv_tau_h * kInvCs2;
     m.Fhat = -rcp * (ux * qx + uy * qy) * k;
     return m;
@@ -239,65 +241,124 @@ __device__ __forceinline__ void node_equilibria_(float phi, float rho, float ux,
     heq[0] = T - sh;
 }
 
-// BGK collisions of the three LBEs at one node (Eq. 14, Sec. 3.1 NS LBE, Eq. 28
-// collision part).  Overwrites f, g, h with the post-collision populations.
-__device__ __forceinline__ void node_collide(const DevParams& P, const Macro& m, float* f, float* g, float* h)
+// Two-relaxation-time collisions of g and h (the stability extension of Sec. 3): with
+// X^{+/-} = (X_i +/- X_opp(i)) / 2, the even part relaxes at om_p, the odd part at om_m,
+// (tau_p - 1/2)(tau_m - 1/2) = Lambda; the viscosity stays on the even part of g
+// (tau_p = tau_g), the conductivity on the odd part of h (tau_m = tau_h).
+__device__ __forceinline__ void node_collide_trt_gh(const DevParams& P, const Macro& m, float* g, float* h)
 {
     const float ux = m.ux, uy = m.uy;
-    const float theta = (1.f - m.phi * m.phi) * P.theta_k;
-    const float ax = (m.dpux + kCs2 * m.nx * theta) * kInvCs2;
-    const float ay = (m.dpuy + kCs2 * m.ny * theta) * kInvCs2;
     const float FxC = m.Fx * kInvCs2, FyC = m.Fy * kInvCs2;
     const float Fh = m.Fhat;
-    float feq[9], geq[9], heq[9];
+    float feq[9], geq[9], heq[9], Gs[9];
     node_equilibria_(m.phi, m.rho, ux, uy, m.p, m.T, feq, geq, heq);
-    float Gs[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float cu = cx(i) * ux + cy(i) * uy;
-        // Allen-Cahn with source R_i
-        const float Ri = wq(i) * (cx(i) * ax + cy(i) * ay);
-        f[i] = f[i] + (feq[i] - f[i]) * P.inv_tau_phi + P.src_phi * Ri;
-        // Navier-Stokes forcing; its u.grad rho terms cancel:
-        // G_i = w_i [ c_i.(Fs + G)/cs2 + (c_i.u)(c_i.grad rho)/cs2 ]
         const float cg = cx(i) * m.grx + cy(i) * m.gry;
         Gs[i] = wq(i) * (cx(i) * FxC + cy(i) * FyC + cu * cg * kInvCs2);
     }
+    const float og_p = m.inv_tau_g;
+    const float og_m = __frcp_rn(0.5f + P.trt_lambda * __frcp_rn(__frcp_rn(og_p) - 0.5f));
+    const float oh_m = m.inv_tau_h;
+    const float oh_p = __frcp_rn(0.5f + P.trt_lambda * __frcp_rn(__frcp_rn(oh_m) - 0.5f));
+    const float cg_p = 1.f - 0.5f * og_p, cg_m = 1.f - 0.5f * og_m;
+    g[0] = g[0] + (geq[0] - g[0]) * og_p + cg_p * Gs[0];
+    h[0] = h[0] + (heq[0] - h[0]) * oh_p + wq(0) * Fh;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int o = opp(i);
+        if (o < i) continue;  // each pair once
+        const float gp = 0.5f * (g[i] + g[o]), gm = 0.5f * (g[i] - g[o]);
+        const float ep = 0.5f * (geq[i] + geq[o]), em = 0.5f * (geq[i] - geq[o]);
+        const float sp = 0.5f * (Gs[i] + Gs[o]), sm = 0.5f * (Gs[i] - Gs[o]);
+        const float dp = (ep - gp) * og_p + cg_p * sp, dm = (em - gm) * og_m + cg_m * sm;
+        g[i] = g[i] + dp + dm;
+        g[o] = g[o] + dp - dm;
+        const float hp = 0.5f * (h[i] + h[o]), hm = 0.5f * (h[i] - h[o]);
+        const float hep = 0.5f * (heq[i] + heq[o]), hem = 0.5f * (heq[i] - heq[o]);
+        const float hdp = (hep - hp) * oh_p + wq(i) * Fh, hdm = (hem - hm) * oh_m;
+        h[i] = h[i] + hdp + hdm;
+        h[o] = h[o] + hdp - hdm;
+    }
+}
+
+// Collisions of the three LBEs at one node (Eq. 14, Sec. 3.1 NS LBE, Eq. 28 collision
+// part); overwrites f, g, h with the post-collision populations.  BGK q_i* = q_i +
+// om (q_i^eq - q_i) + c S_i is evaluated as (1 - om) q_i + w_i t_i, where t_i collects
+// the relaxed equilibrium and the source of direction i:
+//   f: t_i = om phi + c_i . (3 om phi u + (1 - om/2) a),  R_i = w_i c_i . a,
+//      a = 3 d_t(phi u) + n (1 - phi^2) / (sqrt2 W)
+//   g: t_i = om (3 p - 3/2 rho u.u) + c_i . 3 (om rho u + (1 - om/2) F)
+//            + (c_i.u) (9/2 om rho (c_i.u) + 3 (1 - om/2) (c_i . grad rho))
+//      (G_i = w_i [3 c_i . F + 3 (c_i.u)(c_i . grad rho)], its u.grad rho terms cancel)
+//   h: t_i = om T + Fhat
+// Opposite directions share c_i.u c_i.u and (c_i.u)(c_i.grad rho).  The rest
+// populations of f and h are the remainders that keep sum_i f_i* = phi and
+// sum_i h_i* = T + Fhat exactly in exact arithmetic (the float32 weights sum to
+// 1 + 7.5e-9, which would otherwise create phi and T every step); g_0 enters no
+// moment, its equilibrium is the printed one.
+__device__ __forceinline__ void node_collide(const DevParams& P, const Macro& m, float* f, float* g, float* h)
+{
+    constexpr float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+    const float ux = m.ux, uy = m.uy;
+    // Allen-Cahn
+    {
+        const float om = P.inv_tau_phi, k = 1.f - om;
+        const float theta = (1.f - m.phi * m.phi) * P.theta_k;
+        const float ax = fmaf(3.f, m.dpux, m.nx * theta), ay = fmaf(3.f, m.dpuy, m.ny * theta);
+        const float A = om * m.phi, c3 = 3.f * A;
+        const float Bx = fmaf(c3, ux, P.src_phi * ax), By = fmaf(c3, uy, P.src_phi * ay);
+        const float a1 = w1 * A, bx1 = w1 * Bx, by1 = w1 * By;
+        const float a5 = w5 * A, bp5 = w5 * (Bx + By), bm5 = w5 * (Bx - By);
+        f[1] = fmaf(k, f[1], a1 + bx1);
+        f[3] = fmaf(k, f[3], a1 - bx1);
+        f[2] = fmaf(k, f[2], a1 + by1);
+        f[4] = fmaf(k, f[4], a1 - by1);
+        f[5] = fmaf(k, f[5], a5 + bp5);
+        f[7] = fmaf(k, f[7], a5 - bp5);
+        f[8] = fmaf(k, f[8], a5 + bm5);
+        f[6] = fmaf(k, f[6], a5 - bm5);
+        f[0] = m.phi - (((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
+    }
     if (P.collision == 1) {
-        // two relaxation times (the stability extension of Sec. 3) for g and h: with
-        // X^{+/-} = (X_i +/- X_opp(i)) / 2, the even part relaxes at om_p, the odd part at
-        // om_m, (tau_p - 1/2)(tau_m - 1/2) = Lambda; the viscosity stays on the even part
-        // of g (tau_p = tau_g), the conductivity on the odd part of h (tau_m = tau_h)
-        const float og_p = m.inv_tau_g;
-        const float og_m = __frcp_rn(0.5f + P.trt_lambda * __frcp_rn(__frcp_rn(og_p) - 0.5f));
-        const float oh_m = m.inv_tau_h;
-        const float oh_p = __frcp_rn(0.5f + P.trt_lambda * __frcp_rn(__frcp_rn(oh_m) - 0.5f));
-        const float cg_p = 1.f - 0.5f * og_p, cg_m = 1.f - 0.5f * og_m;
-        g[0] = g[0] + (geq[0] - g[0]) * og_p + cg_p * Gs[0];
-        h[0] = h[0] + (heq[0] - h[0]) * oh_p + wq(0) * Fh;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const int o = opp(i);
-            if (o < i) continue;  // each pair once
-            const float gp = 0.5f * (g[i] + g[o]), gm = 0.5f * (g[i] - g[o]);
-            const float ep = 0.5f * (geq[i] + geq[o]), em = 0.5f * (geq[i] - geq[o]);
-            const float sp = 0.5f * (Gs[i] + Gs[o]), sm = 0.5f * (Gs[i] - Gs[o]);
-            const float dp = (ep - gp) * og_p + cg_p * sp, dm = (em - gm) * og_m + cg_m * sm;
-            g[i] = g[i] + dp + dm;
-            g[o] = g[o] + dp - dm;
-            const float hp = 0.5f * (h[i] + h[o]), hm = 0.5f * (h[i] - h[o]);
-            const float hep = 0.5f * (heq[i] + heq[o]), hem = 0.5f * (heq[i] - heq[o]);
-            const float hdp = (hep - hp) * oh_p + wq(i) * Fh, hdm = (hem - hm) * oh_m;
-            h[i] = h[i] + hdp + hdm;
-            h[o] = h[o] + hdp - hdm;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            g[i] = g[i] + (geq[i] - g[i]) * m.inv_tau_g + m.src_g * Gs[i];
-            // thermal with source w_i Fhat
-            h[i] = h[i] + (heq[i] - h[i]) * m.inv_tau_h + wq(i) * Fh;
-        }
+        node_collide_trt_gh(P, m, g, h);
+        return;
+    }
+    // Navier-Stokes
+    {
+        const float om = m.inv_tau_g, k = 1.f - om, sg = m.src_g;
+        const float orho = om * m.rho;
+        const float P0 = om * fmaf(-1.5f * m.rho, ux * ux + uy * uy, 3.f * m.p);
+        const float Vx = 3.f * fmaf(orho, ux, sg * m.Fx), Vy = 3.f * fmaf(orho, uy, sg * m.Fy);
+        const float K1 = 4.5f * orho, K2 = 3.f * sg;
+        // pair (i, o): t_i = P0 + Q + c_i.V, t_o = P0 + Q - c_i.V, Q = cu (K1 cu + K2 cg)
+        auto pair = [&](int i, int o, float w, float cu, float cg, float cv) {
+            const float base = fmaf(cu, fmaf(K1, cu, K2 * cg), P0);
+            g[i] = fmaf(k, g[i], w * (base + cv));
+            g[o] = fmaf(k, g[o], w * (base - cv));
+        };
+        pair(1, 3, w1, ux, m.grx, Vx);
+        pair(2, 4, w1, uy, m.gry, Vy);
+        pair(5, 7, w5, ux + uy, m.grx + m.gry, Vx + Vy);
+        pair(8, 6, w5, ux - uy, m.grx - m.gry, Vx - Vy);
+        // g_0^eq = (w_0 - 1) p / cs2 + rho w_0 (-u.u / (2 cs2)), G_0 = 0
+        g[0] = fmaf(k, g[0], om * (-(5.f / 3.f) * m.p - (2.f / 3.f) * m.rho * (ux * ux + uy * uy)));
+    }
+    // thermal, source w_i Fhat
+    {
+        const float om = m.inv_tau_h, k = 1.f - om;
+        const float t = fmaf(om, m.T, m.Fhat);
+        const float t1 = w1 * t, t5 = w5 * t;
+        h[1] = fmaf(k, h[1], t1);
+        h[2] = fmaf(k, h[2], t1);
+        h[3] = fmaf(k, h[3], t1);
+        h[4] = fmaf(k, h[4], t1);
+        h[5] = fmaf(k, h[5], t5);
+        h[6] = fmaf(k, h[6], t5);
+        h[7] = fmaf(k, h[7], t5);
+        h[8] = fmaf(k, h[8], t5);
+        h[0] = (m.T + m.Fhat) - (((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8])));
     }
 }
 

@@ -55,15 +55,22 @@ __device__ __forceinline__ RefT ref_pack(float m0, float jx, float jy, RefVals& 
     return q;
 }
 
+// c_i . (vx, vy) for a moving direction i, adding only its nonzero components (after
+// unrolling, i is a constant and the selects fold away)
+__device__ __forceinline__ float cdot(int i, float vx, float vy)
+{
+    const float a = cx(i) > 0 ? vx : -vx, b = cy(i) > 0 ? vy : -vy;
+    return cx(i) == 0 ? b : (cy(i) == 0 ? a : a + b);
+}
 // reference of population i of f or h from its writer's record
 __device__ __forceinline__ float ref_pop(int i, const RefVals& r)
 {
-    return wq(i) * (r.m0 + (float)cx(i) * r.jx + (float)cy(i) * r.jy);
+    return i == 0 ? wq(0) * r.m0 : wq(i) * (r.m0 + cdot(i, r.jx, r.jy));
 }
 // reference of population i of g (r.m0 = p / cs2)
 __device__ __forceinline__ float ref_g(int i, const RefVals& r)
 {
-    return fmaf(wg(i), r.m0, wq(i) * ((float)cx(i) * r.jx + (float)cy(i) * r.jy));
+    return i == 0 ? wg(0) * r.m0 : fmaf(wg(i), r.m0, wq(i) * cdot(i, r.jx, r.jy));
 }
 
 // node that wrote population i at (x, y), whose record is its FP16 reference (for the
@@ -145,20 +152,10 @@ __device__ __forceinline__ void collide_push(const DevParams& P, typename S::ele
     // FP16 reference records of what this node emits (as the decoder sees them)
     RefVals rf{0.f, 0.f, 0.f}, rgv{0.f, 0.f, 0.f}, rh{0.f, 0.f, 0.f};
     if constexpr (kRef<S>) {
-        float jfx = 0.f, jfy = 0.f, jgx = 0.f, jgy = 0.f, jhx = 0.f, jhy = 0.f;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            if (cx(i) != 0) {
-                jfx += (float)cx(i) * f[i];
-                jgx += (float)cx(i) * g[i];
-                jhx += (float)cx(i) * h[i];
-            }
-            if (cy(i) != 0) {
-                jfy += (float)cy(i) * f[i];
-                jgy += (float)cy(i) * g[i];
-                jhy += (float)cy(i) * h[i];
-            }
-        }
+        float jfx, jfy, jgx, jgy, jhx, jhy;
+        dq9_moment1(f, jfx, jfy);
+        dq9_moment1(g, jgx, jgy);
+        dq9_moment1(h, jhx, jhy);
         refB[kRecF * pl + n] = ref_pack(m.phi, jfx * kInvCs2, jfy * kInvCs2, rf);
         refB[kRecG * pl + n] = ref_pack(m.p * kInvCs2, jgx * kInvCs2, jgy * kInvCs2, rgv);
         refB[kRecH * pl + n] = ref_pack(m.T, jhx * kInvCs2, jhy * kInvCs2, rh);
@@ -735,7 +732,8 @@ template <int BX, int BY, class S>
 __global__ void __launch_bounds__(BX * BY, kTmaMinBlocks<S>)
 k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typename S::elem* __restrict__ A,
            typename S::elem* __restrict__ B, float* __restrict__ phiu, const RefT* __restrict__ refA,
-           RefT* __restrict__ refB, int bx0, int by0, int ntbx, int ntby, int* __restrict__ err)
+           RefT* __restrict__ refB, const int2* __restrict__ tiles, int bx0, int by0, int ntbx, int ntby,
+           int* __restrict__ err)
 {
     using L = TmaLayout<BX, BY, S>;
     static_assert(sizeof(RingSmem<BX, BY>) <= 2 * L::STAGE, "general-path tiles reuse the stages");
@@ -763,38 +761,16 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     }
     __syncthreads();
 
-    // Tile list: first the rectangle's rows and columns that touch the lattice boundary
-    // (only its first and last row and column can), then the others row by row, so that
-    // no CTA's round-robin share holds more than one of the slower boundary tiles while
-    // fewer of them than CTAs exist.
-    auto row_edge = [&](int b) { return b * BY <= 1 || b * BY + BY >= P.ny - 1; };
-    auto col_edge = [&](int b) { return b * BX <= 1 || b * BX + BX >= P.nx - 1; };
-    const bool fre = row_edge(by0), lre = ntby > 1 && row_edge(by0 + ntby - 1);
-    const bool fce = col_edge(bx0), lce = ntbx > 1 && col_edge(bx0 + ntbx - 1);
-    const int nr = (int)fre + (int)lre, nc = (int)fce + (int)lce;
-    const int rlo = by0 + (int)fre, nrest = ntby - nr;  // rows that are not boundary rows
-    const int clo = bx0 + (int)fce, ncrest = ntbx - nc;
-    auto tile_of = [&](int t, int& bx, int& by) {
-        if (t < nr * ntbx) {
-            bx = bx0 + t % ntbx;
-            by = (t / ntbx == 0 && fre) ? by0 : by0 + ntby - 1;
-            return;
-        }
-        t -= nr * ntbx;
-        if (t < nc * nrest) {
-            by = rlo + t % nrest;
-            bx = (t / nrest == 0 && fce) ? bx0 : bx0 + ntbx - 1;
-            return;
-        }
-        t -= nc * nrest;
-        bx = clo + t % ncrest;
-        by = rlo + t / ncrest;
+    // the host-built tile list: boundary tiles of the rectangle first, then row by row
+    auto tile_of = [&](int t, int& x0, int& y0) {
+        const int2 v = __ldg(tiles + t);
+        x0 = v.x;
+        y0 = v.y;
     };
 
     auto issue = [&](int t, int s) {
-        int bx, by;
-        tile_of(t, bx, by);
-        const int x0 = bx * BX, y0 = by * BY;
+        int x0, y0;
+        tile_of(t, x0, y0);
         tma_issue_tile<BX, BY, S>(maps, dsm + s * L::STAGE, &bar[s], x0, y0);
     };
 
@@ -811,9 +787,8 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
         // every thread waits for the stage itself; a thread whose wait ran out reads
         // stale (in-bounds) shared memory until the block votes at the next barrier
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-        int bx, by;
-        tile_of(t, bx, by);
-        const int x0 = bx * BX, y0 = by * BY;
+        int x0, y0;
+        tile_of(t, x0, y0);
         // the tile body is compiled twice: for tiles touching the lattice boundary and
         // for all others, which keep the plain interior code
         auto on_abort = [&]() {

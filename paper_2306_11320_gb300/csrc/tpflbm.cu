@@ -13,6 +13,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "../../include/tpflbm.h"
 #include "handle.h"
@@ -482,7 +483,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 long long plane_of(int nx, int ny) { return (((long long)nx * ny + 63) / 64) * 64; }
 
 struct Layout {
-    size_t pop0, pop1, ref0, ref1, phiu, stage, red, err, snap, total;
+    size_t pop0, pop1, ref0, ref1, phiu, stage, red, err, snap, tiles, total;
 };
 
 Layout layout_of(int nx, int ny, int storage)
@@ -501,6 +502,8 @@ Layout layout_of(int nx, int ny, int storage)
     L.red = off; off = align256(off + (kRedMaxBlocks * 8 + 8) * sizeof(double));
     L.err = off; off = align256(off + 256);
     L.snap = off; off = align256(off + 3 * (size_t)pl * 4);
+    // the TMA step kernel's tile list (x0, y0 per tile)
+    L.tiles = off; off = align256(off + (size_t)((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY) * sizeof(int2));
     L.total = off;
     return L;
 }
@@ -671,6 +674,33 @@ void setup_tma(tpflbm_t h)
         else M.ref = M.phiu;
         if (!ok) return;
     }
+    // Tile list: first the rectangle's rows and columns that touch the lattice boundary
+    // (only its first and last row and column can), then the others row by row, so that
+    // no CTA's round-robin share holds more than one of the slower boundary tiles while
+    // fewer of them than CTAs exist.
+    {
+        const int ntbx = h->ntbx, ntby = h->ntby;
+        auto row_edge = [&](int b) { return b * kBY <= 1 || b * kBY + kBY >= ny - 1; };
+        auto col_edge = [&](int b) { return b * kBX <= 1 || b * kBX + kBX >= nx - 1; };
+        const bool fre = row_edge(by_lo), lre = ntby > 1 && row_edge(by_lo + ntby - 1);
+        const bool fce = col_edge(bx_lo), lce = ntbx > 1 && col_edge(bx_lo + ntbx - 1);
+        std::vector<int2> list;
+        list.reserve((size_t)ntbx * ntby);
+        auto add = [&](int bx, int by) { list.push_back(make_int2(bx * kBX, by * kBY)); };
+        const int rlo = by_lo + (int)fre, rhi = by_lo + ntby - 1 - (int)lre;  // rows that are not boundary rows
+        const int clo = bx_lo + (int)fce, chi = bx_lo + ntbx - 1 - (int)lce;
+        if (fre) for (int bx = bx_lo; bx < bx_lo + ntbx; ++bx) add(bx, by_lo);
+        if (lre) for (int bx = bx_lo; bx < bx_lo + ntbx; ++bx) add(bx, by_lo + ntby - 1);
+        if (fce) for (int by = rlo; by <= rhi; ++by) add(bx_lo, by);
+        if (lce) for (int by = rlo; by <= rhi; ++by) add(bx_lo + ntbx - 1, by);
+        for (int by = rlo; by <= rhi; ++by)
+            for (int bx = clo; bx <= chi; ++bx) add(bx, by);
+        if ((long long)list.size() != (long long)ntbx * ntby) return;
+        if (cudaMemcpy(h->tiles, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
     const int smem = 2 * L::STAGE;
     if (cudaFuncSetAttribute(k_step_tma<kBX, kBY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         cudaGetLastError();
@@ -705,6 +735,7 @@ int finish_create(tpflbm_t h, int nx, int ny, const tpflbm_params* p, void* ws, 
     h->red = (double*)(b + L.red);
     h->err = (int*)(b + L.err);
     h->snap = (float*)(b + L.snap);
+    h->tiles = (int2*)(b + L.tiles);
     if (cudaMemset(h->err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "cudaMemset");
     if (p->storage == TPF_STORAGE_FP16) setup_tma<StoreF16>(h);
     else setup_tma<StoreF32>(h);
@@ -722,7 +753,8 @@ void launch_step(tpflbm_t h)
     if (h->tma) {
         using L = TmaLayout<kBX, kBY, S>;
         k_step_tma<kBX, kBY, S><<<h->grid_tma, kBX * kBY, 2 * L::STAGE, h->stream>>>(
-            P, h->maps[c], A, B, h->phiu, h->ref[c], h->ref[c ^ 1], h->bx0, h->by0, h->ntbx, h->ntby, h->err);
+            P, h->maps[c], A, B, h->phiu, h->ref[c], h->ref[c ^ 1], h->tiles, h->bx0, h->by0, h->ntbx, h->ntby,
+            h->err);
     } else {
         dim3 grd((P.nx + kBX - 1) / kBX, (P.ny + kBY - 1) / kBY);
         k_step_general<kBX, kBY, S><<<grd, kBX * kBY, 0, h->stream>>>(P, A, B, h->phiu, h->ref[c], h->ref[c ^ 1]);
@@ -930,6 +962,12 @@ int tpflbm_step(tpflbm_t h, long long nsteps)
     TPF_CUDA(h, cudaGetLastError());
     h->t += nsteps;
     return TPF_OK;
+}
+
+int tpflbm_status(tpflbm_t h)
+{
+    if (!h) return TPF_ERR_INVALID_ARG;
+    return check_err(h);
 }
 
 int tpflbm_get_fields(tpflbm_t h, float* phi, float* ux, float* uy, float* p, float* T)

@@ -42,26 +42,33 @@ def _horizons(lat, ref, storage, tag, bubbles=False):
         errs = check_fields(lat.fields(), fp64, _tol(storage), fl)
         print(tag, "storage", storage, "steps", steps, {k: "%.2e (bound %.2e)" % v for k, v in errs.items()})
         if bubbles:
-            _bubbles_vs_oracle(lat, fp64, storage)
+            _bubbles_vs_oracle(lat, fp64, fl, storage)
     d = lat.diagnostics()
     assert d["nonfinite"] == 0
 
 
-def _bubbles_vs_oracle(lat, fp64, storage):
+def _bubbles_vs_oracle(lat, fp64, fl, storage):
     """Sec. 4.3 per-bubble position and velocity from the device labelling against the
-    flood-fill reference on the FP64 oracle's fields: the same two bubbles, centroids
-    within 1e-3 (FP32) or 1e-2 (FP16) nodes, velocities within the field bound."""
+    flood-fill reference on the FP64 oracle's fields: the same two bubbles, node counts
+    within a few interface nodes, centroid and velocity within max(a floor, 3 x the
+    float32 oracle's own deviation) like the fields (floors: 1e-4 nodes and 1e-5 of the
+    bubble speed for FP32, 1e-2 nodes and 5e-3 for FP16)."""
     from oracle.bubbles_ref import bubbles as ref_bubbles
 
     g = lat.bubbles()
     r = ref_bubbles(fp64["phi"], fp64["ux"], fp64["uy"])
-    assert len(g) == len(r) == 2, (g, r)
-    tol_x = 1e-2 if storage else 1e-3
-    for a, b in zip(g, r):
+    r32 = ref_bubbles(fl["phi"], fl["ux"], fl["uy"])
+    assert len(g) == len(r) == len(r32) == 2, (g, r)
+    x_floor, u_floor = (1e-2, 5e-3) if storage else (1e-4, 1e-5)
+    for a, b, c in zip(g, r, r32):
         assert abs(a["nodes"] - b["nodes"]) <= 4, (a, b)
-        assert abs(a["x_b"] - b["x_b"]) < tol_x and abs(a["y_b"] - b["y_b"]) < tol_x, (a, b)
+        for k in ("x_b", "y_b"):
+            bound = max(x_floor, 3.0 * abs(c[k] - b[k]))
+            assert abs(a[k] - b[k]) <= bound, (k, a[k], b[k], bound)
+        speed = max(abs(b["u_b"]), abs(b["v_b"]))
         for k in ("u_b", "v_b"):
-            assert abs(a[k] - b[k]) <= (1e-2 if storage else 1e-3) * max(abs(b["u_b"]), 1e-9), (k, a, b)
+            bound = max(u_floor * speed, 3.0 * abs(c[k] - b[k]))
+            assert abs(a[k] - b[k]) <= bound, (k, a[k], b[k], bound)
     print("bubbles", [(round(b["x_b"], 3), "%.3e" % b["u_b"]) for b in g])
 
 
