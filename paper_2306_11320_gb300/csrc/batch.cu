@@ -197,10 +197,10 @@ k_step_batch_tma(const BatchTmaInst* __restrict__ inst, const int4* __restrict__
         const E* A = (const E*)D.pop[parity];
         E* B = (E*)D.pop[parity ^ 1];
         RefT* refB = D.ref[parity ^ 1];
-        if (cur.w ? tma_tile<BX, BY, S, true>(P, A, B, D.phiu, refB, st, sm, x0, y0, cur.z, ok, on_abort,
-                                              after_ring)
-                  : tma_tile<BX, BY, S, false>(P, A, B, D.phiu, refB, st, sm, x0, y0, 0, ok, on_abort,
-                                               after_ring))
+        if (cur.w ? tma_tile<BX, BY, S, true, false>(P, A, B, D.phiu, refB, st, sm, x0, y0, cur.z, ok, on_abort,
+                                                     after_ring)
+                  : tma_tile<BX, BY, S, false, false>(P, A, B, D.phiu, refB, st, sm, x0, y0, 0, ok, on_abort,
+                                                      after_ring))
             return;
         if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
         cur = nxt;

@@ -548,7 +548,7 @@ __device__ __noinline__ void seam_patch(unsigned char* st, int seam, const typen
 // column of a periodic x seam comes from A first.  EDGE and seam must be the
 // same on every thread and must not come from a staged P (it is not to be trusted
 // before the vote).
-template <int BX, int BY, class S, bool EDGE, class OnAbort, class AfterRing>
+template <int BX, int BY, class S, bool EDGE, bool PRELOAD, class OnAbort, class AfterRing>
 __device__ __forceinline__ bool tma_tile(const DevParams& P, const typename S::elem* __restrict__ A,
                                          typename S::elem* __restrict__ B, float* __restrict__ phiu,
                                          RefT* __restrict__ refB,
@@ -635,6 +635,26 @@ __device__ __forceinline__ bool tma_tile(const DevParams& P, const typename S::e
         sm.T[kown] = sh;
         sm.irc[kown] = __frcp_rn(fmaf(P.rcp_b, clamp1(sf), P.rcp_a));
     }
+    // PRELOAD (tiles without boundary nodes): the rest of the tile's reads of the stage,
+    // done before the ring barrier so that the stage is free after it: the destinations'
+    // pre-collision h_i for the push (each came from this node, so for FP16 its
+    // reference is this node's record) and the previous (phi u)
+    constexpr bool kPre = PRELOAD && !EDGE;
+    float hold_r[9], pu_x = 0.f, pu_y = 0.f;
+    RefVals rown_h{0.f, 0.f, 0.f};
+    (void)hold_r;
+    if constexpr (kPre) {
+        if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int kd = kown + cy(i) * SX + cx(i);
+            float r = 0.f;
+            if constexpr (kRef<S>) r = ref_pop(i, rown_h);
+            hold_r[i] = S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
+        }
+        pu_x = sU[ty * BX + tx];
+        pu_y = sU[(BY + ty) * BX + tx];
+    }
     // ring: 2 (BX + BY) + 4 nodes, one zeroth moment (f or h) per thread
     if (tid < 2 * kRing) {
         const int r = tid < kRing ? tid : tid - kRing;
@@ -699,19 +719,25 @@ __device__ __forceinline__ bool tma_tile(const DevParams& P, const typename S::e
         phin[i] = sm.phi[k];
         Tn[i] = sm.T[k];
     }
-    const Macro m = node_macro(P, f, g, h, phin, Tn, sU[ty * BX + tx], sU[(BY + ty) * BX + tx]);
+    if constexpr (!kPre) {
+        pu_x = sU[ty * BX + tx];
+        pu_y = sU[(BY + ty) * BX + tx];
+    }
+    const Macro m = node_macro(P, f, g, h, phin, Tn, pu_x, pu_y);
     phiu[n] = m.phi * m.ux;
     phiu[pl + n] = m.phi * m.uy;
-    RefVals rown_h{0.f, 0.f, 0.f};
-    (void)rown_h;
-    if constexpr (kRef<S>) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
+    if constexpr (kRef<S> && !kPre) rown_h = ref_unpack(sR[(kRecH * L::RH + ly + 1) * L::RW + lx + 3]);
     collide_push<S, SX>(
         P, B, refB, x, y, kown, !edge, m, f, g, h,
         [&](int i, int kd) {
-            // h_i of destination kd came from this node: its reference is this node's record
-            float r = 0.f;
-            if constexpr (kRef<S>) r = ref_pop(i, rown_h);
-            return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
+            if constexpr (kPre) {
+                return hold_r[i];  // interior tiles push only to kd = own + c_i
+            } else {
+                // h_i of destination kd came from this node: its reference is this node's record
+                float r = 0.f;
+                if constexpr (kRef<S>) r = ref_pop(i, rown_h);
+                return S::lds(sH, (i * L::FH + kd / SX) * L::FW + kd % SX - 1 + L::XP, P.is_h, r);
+            }
         },
         [&](int kd) { return sm.irc[kd]; });
     return false;
@@ -739,14 +765,14 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     static_assert(sizeof(RingSmem<BX, BY>) <= 2 * L::STAGE, "general-path tiles reuse the stages");
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar[2];
-    // Where a tile's copies are issued.  FP32: at the top of the tile before, with a
-    // block barrier closing every tile.  FP16: after the ring barrier of the tile
-    // before, when every warp is done with the stage, and no closing barrier, so warps
-    // may run into the next tile while others still push; phi, T and 1/(rho c_p) are
-    // then double buffered.  Measured on the 2048 x 512 channel (us per step, same
-    // results bit for bit): FP32 47.1 against 48.9, FP16 58.0 against 60.4.
-    constexpr bool kLate = kRef<S>;
-    __shared__ PhiSmem<BX, BY> smb[kLate ? 2 : 1];
+    // Where a tile's copies are issued: tile t + 2 (this CTA's after next) goes into the
+    // stage of tile t as soon as tile t no longer reads it.  Tiles without boundary
+    // nodes read everything they need from the stage before their ring barrier
+    // (PRELOAD), so their stage is refilled right after it and the tile ends without a
+    // block barrier; boundary tiles end with one and refill after it.  phi, T and
+    // 1/(rho c_p) are double buffered: a warp may start the next tile while others still
+    // push (it cannot get two tiles ahead: the next ring barrier waits for them).
+    __shared__ PhiSmem<BX, BY> smb[2];
 
     const int ntma = ntbx * ntby;  // TMA tiles: bx in [bx0, bx0 + ntbx), by in [by0, by0 + ntby)
     const int tilesx = (P.nx + BX - 1) / BX, tilesy = (P.ny + BY - 1) / BY;
@@ -761,34 +787,44 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     }
     __syncthreads();
 
-    // the host-built tile list: boundary tiles of the rectangle first, then row by row
-    auto tile_of = [&](int t, int& x0, int& y0) {
-        const int2 v = __ldg(tiles + t);
+    // The host-built tile list (boundary tiles of the rectangle first, then row by
+    // row): this CTA's first kTileCache entries are read once into shared memory here,
+    // so that no tile waits on a global load for its own coordinates.
+    constexpr int kTileCache = 64;
+    __shared__ int2 my_tiles[kTileCache];
+    for (int k = tid; k < kTileCache; k += BX * BY) {
+        const int t = blockIdx.x + k * gridDim.x;
+        my_tiles[k] = t < ntma ? __ldg(tiles + t) : make_int2(0, 0);
+    }
+    __syncthreads();
+    // tile t = blockIdx.x + k gridDim.x is this CTA's k-th
+    auto tile_of = [&](int t, int k, int& x0, int& y0) {
+        const int2 v = k < kTileCache ? my_tiles[k] : __ldg(tiles + t);
         x0 = v.x;
         y0 = v.y;
     };
 
-    auto issue = [&](int t, int s) {
+    auto issue = [&](int t, int k, int s) {
         int x0, y0;
-        tile_of(t, x0, y0);
+        tile_of(t, k, x0, y0);
         tma_issue_tile<BX, BY, S>(maps, dsm + s * L::STAGE, &bar[s], x0, y0);
     };
 
     int it = 0;
     int t = blockIdx.x;
-    if (t < ntma && tid == 0) issue(t, 0);
+    if (tid == 0) {
+        if (t < ntma) issue(t, 0, 0);
+        if (t + (int)gridDim.x < ntma) issue(t + gridDim.x, 1, 1);
+    }
     for (; t < ntma; t += gridDim.x, ++it) {
         const int s = it & 1;
-        const int tn = t + gridDim.x;
-        if constexpr (!kLate) {
-            if (tn < ntma && tid == 0) issue(tn, s ^ 1);
-        }
-        PhiSmem<BX, BY>& sm = smb[kLate ? s : 0];
+        const int tn = t + gridDim.x, t2 = t + 2 * gridDim.x;
+        PhiSmem<BX, BY>& sm = smb[s];
         // every thread waits for the stage itself; a thread whose wait ran out reads
         // stale (in-bounds) shared memory until the block votes at the next barrier
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
         int x0, y0;
-        tile_of(t, x0, y0);
+        tile_of(t, it, x0, y0);
         // the tile body is compiled twice: for tiles touching the lattice boundary and
         // for all others, which keep the plain interior code
         auto on_abort = [&]() {
@@ -796,24 +832,24 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
                 atomicExch(err, 1);
                 // let this CTA's copies in flight land (bounded) before leaving
                 mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-                if (!kLate && tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+                if (tn < ntma) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
             }
         };
-        auto after_ring = [&]() {
-            if constexpr (kLate) {
-                // every warp has finished the tile before, whose stage is s ^ 1
-                if (tn < ntma && tid == 0) issue(tn, s ^ 1);
-            }
+        auto refill = [&]() {
+            if (t2 < ntma && tid == 0) issue(t2, it + 2, s);
         };
+        auto no_refill = [&]() {};
         unsigned char* st = dsm + s * L::STAGE;
         const bool edge_tile = x0 <= 1 || x0 + BX >= P.nx - 1 || y0 <= 1 || y0 + BY >= P.ny - 1;
         const int seam = seam_side<BX>(P, x0);
-        if (edge_tile ? tma_tile<BX, BY, S, true>(P, A, B, phiu, refB, st, sm, x0, y0, seam, ok, on_abort,
-                                                  after_ring)
-                      : tma_tile<BX, BY, S, false>(P, A, B, phiu, refB, st, sm, x0, y0, 0, ok, on_abort,
-                                                   after_ring))
+        if (edge_tile) {
+            if (tma_tile<BX, BY, S, true, false>(P, A, B, phiu, refB, st, sm, x0, y0, seam, ok, on_abort, no_refill))
+                return;
+            __syncthreads();  // every warp is done with stage s
+            refill();
+        } else if (tma_tile<BX, BY, S, false, true>(P, A, B, phiu, refB, st, sm, x0, y0, 0, ok, on_abort, refill)) {
             return;
-        if constexpr (!kLate) __syncthreads();  // stage s and sm are free for the next copies
+        }
     }
 
     // the tiles outside the TMA rectangle (periodic seams, ragged edges) through the

@@ -91,17 +91,23 @@ def test_pack_unpack_with_base():
 
 
 def test_trained_network_shortens_time_to_steady():
-    """The committed network on two held-out channels with k = 1 (the slow ones): the
-    warm start reaches r < 1e-7 in less than half the cold start's steps, and both
-    runs end in the same state to within the slow-mode drift the residual allows."""
+    """The committed network on every held-out channel (20 draws of conductivity ratio,
+    layer-height ratio and wall wavenumber), wall time to r < 1e-8 from the cold and
+    from the warm start: every warm run converges within 800k steps, no warm start is
+    slower than its cold start, the aggregate wall-time ratio is at least 2, and both
+    runs end in the same phase and temperature fields to within the slow-mode drift
+    the residual criterion allows."""
     from paper_2306_11320_gb300 import warmstart as WS
 
     net, norm, meta = WS.load(WS.WEIGHTS)
-    insts = [i for i in WS.held_out(meta) if i["k"] == 1][:2]
-    assert len(insts) == 2
-    rows = WS.compare(net, norm, insts, tols=(1e-7,), max_steps=800_000, log=lambda m: None)
+    insts = WS.held_out(meta)
+    assert len(insts) == 20
+    rows = WS.compare(net, norm, insts, tols=(1e-8,), max_steps=800_000, log=lambda m: None)
+    summ = WS.summarize(rows, (1e-8,))
+    print("aggregate", summ["aggregate_1e-08"], "per instance", summ["speedup_time_1e-08"])
     for r in rows:
-        assert r["warm_steps_1e-07"] is not None
-        cold = r["cold_steps_1e-07"] or 800_000
-        assert 2 * r["warm_steps_1e-07"] < cold, r
+        print({k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items() if k != "final_rel_l2"})
+        assert r["warm_steps_1e-08"] is not None, r
+        assert r["warm_s_1e-08"] <= r["cold_s_1e-08"], r
         assert r["final_rel_l2"]["T"] < 1e-3 and r["final_rel_l2"]["phi"] < 1e-3, r
+    assert summ["aggregate_1e-08"]["ratio"] >= 2.0, summ

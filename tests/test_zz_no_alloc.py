@@ -94,7 +94,7 @@ class _DeviceBytes:
     """A raw device address seen by torch as a uint8 array (__cuda_array_interface__)."""
 
     def __init__(self, addr, nbytes):
-        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (addr, True),
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (addr, False),
                                          "version": 3, "strides": None}
 
 
