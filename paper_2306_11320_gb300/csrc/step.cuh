@@ -787,19 +787,8 @@ k_step_tma(const DevParams P, const __grid_constant__ TmaMaps maps, const typena
     }
     __syncthreads();
 
-    // The host-built tile list (boundary tiles of the rectangle first, then row by
-    // row): this CTA's first kTileCache entries are read once into shared memory here,
-    // so that no tile waits on a global load for its own coordinates.
-    constexpr int kTileCache = 64;
-    __shared__ int2 my_tiles[kTileCache];
-    for (int k = tid; k < kTileCache; k += BX * BY) {
-        const int t = blockIdx.x + k * gridDim.x;
-        my_tiles[k] = t < ntma ? __ldg(tiles + t) : make_int2(0, 0);
-    }
-    __syncthreads();
-    // tile t = blockIdx.x + k gridDim.x is this CTA's k-th
     auto tile_of = [&](int t, int k, int& x0, int& y0) {
-        const int2 v = k < kTileCache ? my_tiles[k] : __ldg(tiles + t);
+        const int2 v = __ldg(tiles + t);
         x0 = v.x;
         y0 = v.y;
     };
