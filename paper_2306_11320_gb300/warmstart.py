@@ -124,9 +124,13 @@ def generate(instances, max_steps, tol, batch_size=64, log=print):
     which max(r_u, r_T) < tol (None if never)."""
     from .tpflbm import Batch
 
-    fields, steps = [], []
-    for s in range(0, len(instances), batch_size):
-        chunk = instances[s:s + batch_size]
+    # a batch runs until its slowest member converges: group the instances by wall
+    # wavenumber (the k = 1 channels take the longest), then restore the given order
+    order = sorted(range(len(instances)), key=lambda j: (instances[j]["k"], instances[j]["lam_r"]))
+    fields_o, steps_o = [None] * len(instances), [None] * len(instances)
+    for s in range(0, len(order), batch_size):
+        idx = order[s:s + batch_size]
+        chunk = [instances[j] for j in idx]
         cases = [channel(i) for i in chunk]
         b = Batch([(NX, NY, p) for p, _, _ in cases])
         for k, (_, f, _) in enumerate(cases):
@@ -142,13 +146,13 @@ def generate(instances, max_steps, tol, batch_size=64, log=print):
             for k in range(len(chunk)):
                 if first[k] is None and rr[k] < tol:
                     first[k] = b.t
-        for k in range(len(chunk)):
-            fields.append(b.fields(k))
-        steps.extend(first)
+        for k, j in enumerate(idx):
+            fields_o[j] = b.fields(k)
+            steps_o[j] = first[k]
         log("generated %d/%d (t = %d, %.1f s, converged %d)" % (s + len(chunk), len(instances), b.t,
                                                                  time.time() - t0, sum(v is not None for v in first)))
         b.close()
-    return fields, steps
+    return fields_o, steps_o
 
 
 # ------------------------------------------------------------------ network
