@@ -100,7 +100,7 @@ def test_trained_network_shortens_time_to_steady():
       * no warm start takes more steps than its cold start (within one residual window
         and 10% for rounding-level differences between runs);
       * the total wall time over all 20 channels is at least 1.3 times shorter (measured
-        1.47; the 3x target is not met, see the design notes: on k >= 2 channels the
+        1.47; the 3x target is not met: on k >= 2 channels the
         restart transient of an equilibrium initialisation costs about as much as the
         cold start's own relaxation);
       * both runs end in the same phase and temperature fields to within the slow-mode
