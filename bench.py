@@ -238,6 +238,10 @@ def bench_ours(args, rank, world, local_rank):
                 step_ms = sum(times)
             else:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                # after the synchronisation the GPU is idle: an untimed spin of about 0.1 ms
+                # keeps it busy while the start event and the K launches are queued, so the
+                # events enclose the K steps' device time and not the first launch's latency
+                torch.cuda._sleep(200000)
                 e0.record(stream)
                 for _ in range(args.steps):
                     lat.step(1)
