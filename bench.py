@@ -13,7 +13,10 @@ finds at most the tail of the previous step's writes in L2 (ncu: DRAM reads per
 launch equal the algorithmic reads).  With --flush a 256 MiB write runs between
 timed steps instead, outside per-step events (that write leaves up to the whole L2
 dirty for the next step to write back).  Metric: lattice updates per second (MLUPS,
-one update = one node through all three LBEs), whole job.  Prints one JSON line.
+one update = one node through all three LBEs), whole job.  At N = 1 the line also
+carries the metric's second half, `time_to_steady`: wall time to a steady-state
+residual of 1e-8 from the cold start and from the learned warm start on the 20
+held-out 512 x 128 channels (--no-steady skips it).  Prints one JSON line.
 
 N > 1 (torchrun, one rank per GPU): independent replicas (the path has no
 data-path exchange); value = all ranks' updates / max-over-ranks time.
@@ -191,6 +194,18 @@ def bench_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_to_steady(instances=None, log=lambda m: None):
+    """Cold against learned warm start on the held-out warm-start channels (512 x 128
+    heated microchannel), wall time to max(r_u, r_T) < 1e-8 with r every RESID_K steps,
+    at most 800k steps; returns (rows, summary) of warmstart.compare/summarize."""
+    from paper_2306_11320_gb300 import warmstart as WS
+
+    net, norm, meta = WS.load(WS.WEIGHTS)
+    insts = WS.held_out(meta, instances)
+    rows = WS.compare(net, norm, insts, tols=(1e-8,), max_steps=800_000, log=log)
+    return rows, WS.summarize(rows, (1e-8,)), meta
+
+
 def bench_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -281,6 +296,16 @@ def bench_ours(args, rank, world, local_rank):
         mlups, steps, el, cores = run_oracle_sample(CPU_SAMPLE_SECONDS)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": "%d FP64 oracle steps of the %dx%d bubble channel (%.1f s)" % (steps, NX, NY, el)}
+    steady = None
+    if world == 1 and not args.no_steady:
+        # the metric's second half: time to steady state, plain against learned warm start
+        rows, summ, meta = time_to_steady()
+        agg = summ["aggregate_1e-08"]
+        steady = {"workload": "warmstart_512x128", "instances": len(rows), "tol": 1e-8, "max_steps": 800_000,
+                  "cold_s": agg["cold_s"], "warm_s": agg["warm_s"], "ratio": agg["ratio"],
+                  "cold_unconverged": agg["cold_unconverged"], "warm_unconverged": agg["warm_unconverged"],
+                  "per_instance_median": summ["speedup_time_1e-08"]["median"], "target": ">= 3x",
+                  "train_instances": meta["train"]}
     field_bytes = 5 * 4 * NX * NY
     line = {
         "metric": "coupled-LBM MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -302,6 +327,7 @@ def bench_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "check": {"nonfinite": diag["nonfinite"], "sum_phi": diag["sum_phi"]},
+        "time_to_steady": steady,
     }
     print(json.dumps(line), flush=True)
 
@@ -385,14 +411,12 @@ def bench_warmstart(args, rank, world, local_rank):
     from paper_2306_11320_gb300 import warmstart as WS
 
     torch.cuda.set_device(local_rank)
-    net, norm, meta = WS.load(WS.WEIGHTS)
-    insts = WS.held_out(meta, args.instances)
     tol, max_steps = 1e-8, 800_000
     with ClockSampler(local_rank) as clk:
-        rows = WS.compare(net, norm, insts, tols=(tol,), max_steps=max_steps, log=lambda m: None)
+        rows, summ, meta = time_to_steady(args.instances)
+    insts = rows
     if rank != 0:
         return
-    summ = WS.summarize(rows, (tol,))
     agg = summ["aggregate_1e-08"]
     line = {
         "metric": "time-to-steady speed-up (cold / learned warm start)", "value": agg["ratio"], "unit": "x",
@@ -475,6 +499,8 @@ def main():
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-steady", action="store_true",
+                    help="skip the time-to-steady comparison (cold against learned warm start) of the default line")
     ap.add_argument("--flush", action="store_true",
                     help="write 256 MiB between timed steps (per-step events) instead of timing steps back to back")
     ap.add_argument("--workload", choices=("bubbles", "ensemble", "warmstart", "cpu"), default="bubbles",

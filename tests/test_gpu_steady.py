@@ -2,7 +2,9 @@
 with one computed from read-back fields, and a heated microchannel converges to
 the closed-form regime's steady state (the residual decays to 1e-8; the slowest
 mode is the relaxation of the interface deformation, e-folding in about
-(L / 2 pi)^2 / M_phi = 4k steps)."""
+(L / 2 pi)^2 / M_phi = 4k steps).  The residual is the mean change per step over its
+window K, and its float32 noise floor falls as 1/K: over 100 steps it sits near 1e-7
+on this channel, over 4000 steps well below 1e-8, so the convergence check uses 4000."""
 import numpy as np
 import pytest
 
@@ -41,9 +43,10 @@ def test_microchannel_reaches_residual_1e8():
     lat.init(**{k: v.astype(np.float32) for k, v in f.items()})
     lat.residual(10.0)
     history = []
-    for _ in range(1500):
-        lat.step(100)
-        ru, rT, _ = lat.residual(10.0)
+    for _ in range(50):
+        lat.step(4000)
+        ru, rT, K = lat.residual(10.0)
+        assert K == 4000
         history.append(max(ru, rT))
         if history[-1] < 1e-8:
             break
