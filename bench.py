@@ -253,10 +253,11 @@ def bench_ours(args, rank, world, local_rank):
                 step_ms = sum(times)
             else:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                # after the synchronisation the GPU is idle: an untimed spin of about 0.1 ms
+                # after the synchronisation the GPU is idle: an untimed spin (about 0.2 s, so
+                # that the clock sampler also sees the GPU busy next to a short timed region)
                 # keeps it busy while the start event and the K launches are queued, so the
                 # events enclose the K steps' device time and not the first launch's latency
-                torch.cuda._sleep(200000)
+                torch.cuda._sleep(400_000_000)
                 e0.record(stream)
                 for _ in range(args.steps):
                     lat.step(1)
@@ -325,7 +326,7 @@ def bench_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": field_bytes / args.steps,
                 "d2h_bytes_per_step": field_bytes / args.steps + 4},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
+        "clocks": dict(clk.summary(), window="timed region and the 0.2 s untimed spin before it"),
         "check": {"nonfinite": diag["nonfinite"], "sum_phi": diag["sum_phi"]},
         "time_to_steady": steady,
     }

@@ -42,30 +42,57 @@ constexpr int kVarBY[kNumVariants] = {4, 8, 16, 4, kStepBY};
 // than at 3; FP16 keeps 2 (at 80 registers it spills)
 template <class S>
 constexpr int kBatchThreadsPerSM = kRef<S> ? 512 : 768;
+// The instance descriptor of a work item is copied word by word by warp 0 (32-bit words;
+// InstDesc is plain data).  The next item's copy is loaded into registers while the
+// current tile runs and stored into the other shared buffer after it, so no tile waits
+// on a global load for its parameters.
+constexpr int kDescWords = (int)(sizeof(InstDesc) / 4);
+constexpr int kDescPerLane = (kDescWords + 31) / 32;
+static_assert(sizeof(InstDesc) % 4 == 0, "descriptor copied in 32-bit words");
+
 template <int BX, int BY, class S>
 __global__ void __launch_bounds__(BX * BY, kBatchThreadsPerSM<S> / (BX * BY) > 0 ? kBatchThreadsPerSM<S> / (BX * BY) : 1)
 k_step_batch(const InstDesc* __restrict__ inst, const int2* __restrict__ work, int nwork, int parity)
 {
     __shared__ RingSmem<BX, BY> sm;
-    __shared__ DevParams P;
-    __shared__ const void* bufs[6];
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int2 item = work[w];
-        if (threadIdx.x == 0) {
-            const InstDesc& d = inst[item.x];
-            P = d.P;
-            bufs[0] = d.pop[parity];
-            bufs[1] = d.pop[parity ^ 1];
-            bufs[2] = d.ref[parity];
-            bufs[3] = d.ref[parity ^ 1];
-            bufs[4] = d.phiu;
+    __shared__ __align__(16) InstDesc dsc[2];
+    const int lane = threadIdx.x;  // warp 0 copies the descriptors
+    uint32_t nxt[kDescPerLane];
+    auto load = [&](int w) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(inst + work[w].x);
+#pragma unroll
+        for (int j = 0; j < kDescPerLane; ++j) {
+            const int k = lane + 32 * j;
+            nxt[j] = k < kDescWords ? __ldg(src + k) : 0u;
         }
+    };
+    auto store = [&](int b) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&dsc[b]);
+#pragma unroll
+        for (int j = 0; j < kDescPerLane; ++j) {
+            const int k = lane + 32 * j;
+            if (k < kDescWords) dst[k] = nxt[j];
+        }
+    };
+    int w = blockIdx.x, b = 0;
+    if (w < nwork && threadIdx.x < 32) {
+        load(w);
+        store(0);
+    }
+    __syncthreads();
+    for (; w < nwork; w += gridDim.x, b ^= 1) {
+        const int2 item = work[w];
+        const int wn = w + gridDim.x;
+        if (wn < nwork && threadIdx.x < 32) load(wn);  // lands while this tile runs
+        const InstDesc& d = dsc[b];
+        const typename S::elem* A = (const typename S::elem*)d.pop[parity];
+        typename S::elem* B = (typename S::elem*)d.pop[parity ^ 1];
+        step_tile_general<BX, BY, S>(d.P, A, B, d.phiu, d.ref[parity], d.ref[parity ^ 1], sm, item.y & 0xffff,
+                                     item.y >> 16);
+        // step_tile_general ends with a barrier: buffer b ^ 1 is free (its tile ended a
+        // barrier ago), and after this one the next descriptor is visible
+        if (wn < nwork && threadIdx.x < 32) store(b ^ 1);
         __syncthreads();
-        const typename S::elem* A = (const typename S::elem*)bufs[0];
-        typename S::elem* B = (typename S::elem*)bufs[1];
-        step_tile_general<BX, BY, S>(P, A, B, (float*)bufs[4], (const RefT*)bufs[2], (RefT*)bufs[3], sm,
-                                     item.y & 0xffff, item.y >> 16);
-        // step_tile_general ends with a barrier: P and bufs are free again
     }
 }
 

@@ -48,7 +48,11 @@ def _batch(members, storage=0, variant=None):
 def test_batch_matches_single_lattices(variant):
     """Each member of the batch evolves as the same lattice stepped alone through the
     single-lattice API (the per-tile code is shared), with the general tile path and
-    with the TMA-staged variant."""
+    with the TMA-staged variant.  The two launches are different kernels, so the
+    compiler may fuse a multiply-add differently in each, and the random states
+    amplify a 1-ulp difference to about 2e-6 of the velocity in 40 steps; a tile run
+    with another lattice's parameters, buffers or tile coordinates is off by O(1).
+    Bound: 1e-5 relative L2 per field, the float32 parity target."""
     from paper_2306_11320_gb300.tpflbm import Lattice
 
     members = _members()
@@ -60,7 +64,7 @@ def test_batch_matches_single_lattices(variant):
         lat.step(40)
         a, c = b.fields(k), lat.fields()
         for n in FIELDS:
-            assert rel_l2(a[n], c[n]) <= 1e-6, (k, n, rel_l2(a[n], c[n]))
+            assert rel_l2(a[n], c[n]) <= 1e-5, (k, n, rel_l2(a[n], c[n]))
 
 
 def test_batch_matches_oracle():
