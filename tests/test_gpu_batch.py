@@ -48,23 +48,32 @@ def _batch(members, storage=0, variant=None):
 def test_batch_matches_single_lattices(variant):
     """Each member of the batch evolves as the same lattice stepped alone through the
     single-lattice API (the per-tile code is shared), with the general tile path and
-    with the TMA-staged variant.  The two launches are different kernels, so the
-    compiler may fuse a multiply-add differently in each, and the random states
-    amplify a 1-ulp difference to about 2e-6 of the velocity in 40 steps; a tile run
-    with another lattice's parameters, buffers or tile coordinates is off by O(1).
-    Bound: 1e-5 relative L2 per field, the float32 parity target."""
+    with the TMA-staged variant.  The two launches are different kernels, and the
+    compiler may fuse a multiply-add differently in each; the small random states
+    amplify such a 1-ulp difference (2e-6 of u_x, 1.2e-5 of phi on the 41 x 19 channel
+    after 40 steps), as much as float32 evaluations that differ only by rounding
+    spread among themselves.  Bound per member and field: max(1e-6, 3 x that spread
+    (tests/fieldcheck.py)); a tile run with another lattice's parameters, buffers or
+    tile coordinates is off by O(1)."""
+    from fieldcheck import float32_spread
     from paper_2306_11320_gb300.tpflbm import Lattice
 
     members = _members()
     b = _batch(members, variant=variant)
-    b.step(40)
+    steps = 40
+    b.step(steps)
     for k, (nx, ny, p, f) in enumerate(members):
         lat = Lattice(nx, ny, p)
         lat.init(**{n: v.astype(np.float32) for n, v in f.items()})
-        lat.step(40)
+        lat.step(steps)
         a, c = b.fields(k), lat.fields()
+        o = OracleSim(nx, ny, p)
+        o.init(**{n: v.astype(np.float32).astype(np.float64) for n, v in f.items()})
+        o.step(steps)
+        spread = float32_spread(nx, ny, p, f, steps, o.fields())
         for n in FIELDS:
-            assert rel_l2(a[n], c[n]) <= 1e-5, (k, n, rel_l2(a[n], c[n]))
+            bound = max(1e-6, 3.0 * spread[n])
+            assert rel_l2(a[n], c[n]) <= bound, (k, n, rel_l2(a[n], c[n]), bound)
 
 
 def test_batch_matches_oracle():
