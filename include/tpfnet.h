@@ -26,6 +26,19 @@ extern "C" {
 int tpfnet_conv3x3(const void *x, int N, int H, int W, int Cin, const void *wt, const float *bias, int Cout,
                    int relu, void *y, void *stream);
 
+/* Which kernel tpfnet_conv3x3 (and tpfnet_conv3x3_dgrad, with Cin and Cout swapped)
+ * runs for a shape, given 16-byte aligned tensors: the width in output channels of the
+ * tcgen05 kernel's tiles (32, 64, 128 or 256), or 0 for the mma.sync kernel.  The
+ * tcgen05 kernel takes pixel blocks of 128 = BW x BH with BW = min(W, 128) dividing
+ * both 128 and W and BH dividing H; it stages operands with TMA and accumulates in
+ * tensor memory. */
+int tpfnet_conv3x3_tcgen05(int N, int H, int W, int Cin, int Cout);
+
+/* TPF_OK, or TPF_ERR_TIMEOUT once a bounded wait of the tcgen05 convolution has run
+ * out in this process (its output is then not to be trusted; the flag stays set);
+ * TPF_ERR_CUDA if the flag cannot be read.  Synchronises with the device. */
+int tpfnet_status(void);
+
 /* Data gradient of conv3x3: dx = conv3x3 of dz (the gradient at the convolution's
  * output, ReLU mask already applied) with the flipped, transposed weights, which are
  * written to wflip (9 * Cin * Cout bf16 of caller scratch). */

@@ -4,8 +4,10 @@
 // upsampling, channel concatenation, the 1x1 head, the MSE loss and Adam.
 // Activations are NHWC bfloat16 with channel counts that are multiples of 32;
 // 3x3 weights are [9][Cout][Cin] (tap = (dh + 1) * 3 + (dw + 1)).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "../../include/tpflbm.h"
@@ -110,6 +112,198 @@ k_conv3x3(const bf16* __restrict__ x, int N, int H, int W, int Cin, const bf16* 
             *reinterpret_cast<__nv_bfloat162*>(y + (((size_t)n * H + h) * W + ww) * Cout + co) = o;
         }
     }
+}
+
+// ------------------------------------------------ tcgen05 forward convolution
+//
+// The same convolution on the fifth-generation tensor cores: an implicit GEMM with
+// M = 128 output pixels (a BW x BH block of one image, BW * BH = 128), N = BN output
+// channels and K = 9 taps x Cin.  Operands are staged by TMA in 64-byte-swizzled
+// K-major tiles (32 channels, 64 bytes, per row): the activation tile of a tap is the
+// pixel block shifted by (dh, dw), read through a 4-D tensor map whose out-of-range
+// rows and columns come back as zeros (the padding); the weight tile is BN rows of
+// [9 Cout][Cin].  One thread issues the copies into a ring of kTcStages stages, one
+// thread issues tcgen05.mma (M = 128, N = BN, K = 16, BF16 in, FP32 accumulated in
+// tensor memory) and frees each stage with tcgen05.commit; the four warps then read
+// the accumulator (warp w owns TMEM lanes 32w..32w+31, i.e. pixels), add the bias,
+// apply the ReLU and store bf16.  Every wait is bounded; a wait that runs out sets
+// the error flag and the CTA still releases its tensor memory.
+constexpr int kTcStages = 4;
+constexpr int kTcK = 32;                     // channels per stage (64-byte rows)
+constexpr int kTcABytes = 128 * kTcK * 2;    // activation tile per stage
+__device__ int g_tc_err;                     // a bounded wait of the tcgen05 kernel ran out
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(sa(b)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    atomicExch(&g_tc_err, 1);
+    return false;
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* m, uint64_t* b, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            sa(dst)),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(sa(b))
+        : "memory");
+}
+__device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* m, uint64_t* b, int c0, int c1, int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(sa(dst)),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(sa(b))
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes
+// apart (start address and strides in 16-byte units; descriptor version 1)
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+k_conv3x3_tc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, int H, int W, int Cin,
+             int Cout, int BW, int BH, const float* __restrict__ bias, int relu, bf16* __restrict__ y)
+{
+    static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "TMEM columns: a power of two from 32");
+    constexpr int kBBytes = BN * kTcK * 2;
+    constexpr int kStage = kTcABytes + kBBytes;  // multiple of 1024
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // 1024-byte aligned stages (the swizzle pattern repeats every 512 bytes)
+    unsigned char* st0 = tsm + ((1024 - (sa(tsm) & 1023)) & 1023);
+    const int bpr = W / BW, bpi = bpr * (H / BH);  // pixel blocks per row of blocks, per image
+    const int n = blockIdx.x / bpi, rem = blockIdx.x % bpi;
+    const int h0 = (rem / bpr) * BH, w0 = (rem % bpr) * BW;
+    const int co0 = blockIdx.y * BN;
+    const int kc = Cin / kTcK, ksteps = 9 * kc;
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], 1);
+        }
+        mb_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_base)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // producer: stage k % S holds tap k / kc, channels (k % kc) * 32
+        int issued = 0;
+        for (int k = 0; k < ksteps; ++k) {
+            const int s = k % kTcStages;
+            if (k >= kTcStages && !mb_wait(&empty[s], ((k / kTcStages) - 1) & 1)) break;
+            unsigned char* a = st0 + s * kStage;
+            const int tap = k / kc, c0 = (k % kc) * kTcK;
+            mb_expect_tx(&full[s], kStage);
+            tma_4d(a, &mx, &full[s], c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, n);
+            tma_2d(a + kTcABytes, &mw, &full[s], c0, tap * Cout + co0);
+            issued = k + 1;
+        }
+        // copies still in flight (only after a wait ran out) land before the CTA ends
+        for (int k = issued > kTcStages ? issued - kTcStages : 0; k < issued; ++k)
+            mb_wait(&full[k % kTcStages], (k / kTcStages) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc_idesc(128, BN);
+        for (int k = 0; k < ksteps; ++k) {
+            const int s = k % kTcStages;
+            if (!mb_wait(&full[s], (k / kTcStages) & 1)) break;
+            tc_fence_after();
+            const uint32_t a = sa(st0 + s * kStage), b = a + kTcABytes;
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk) {
+                const uint64_t ad = sw64_desc(a + 32 * kk), bd = sw64_desc(b + 32 * kk);
+                const uint32_t acc = (k | kk) != 0;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            // stage s is free once these MMAs have read it
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             sa(&empty[s]))
+                         : "memory");
+        }
+        // the accumulator is complete once every MMA issued has finished
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(&done))
+                     : "memory");
+    }
+    __syncwarp();
+
+    // epilogue: thread (warp w, lane l) owns pixel 32 w + l of the block
+    mb_wait(&done, 0);
+    tc_fence_after();
+    const int m = warp * 32 + lane;
+    const int hh = h0 + m / BW, ww = w0 + m % BW;
+    bf16* out = y + (((size_t)n * H + hh) * W + ww) * Cout + co0;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 8) {
+        uint32_t r[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[co0 + c + 2 * j] : 0.f);
+            float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[co0 + c + 2 * j + 1] : 0.f);
+            if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            __nv_bfloat162 t;
+            t.x = __float2bfloat16_rn(v0);
+            t.y = __float2bfloat16_rn(v1);
+            o[j] = *reinterpret_cast<uint32_t*>(&t);
+        }
+        *reinterpret_cast<uint4*>(out + c) = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
 // dW[tap][co][ci] += sum_p dz[p][co] x[p + off(tap)][ci], db[co] += sum_p dz[p][co].
@@ -408,6 +602,97 @@ int grid_of(long long count)
 
 int status(cudaError_t e) { return e == cudaSuccess ? TPF_OK : TPF_ERR_CUDA; }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Shapes the tcgen05 convolution takes: pixel blocks of BW x BH = 128 (BW = W up to
+// 128, dividing W; BH dividing H).  BN: the largest of 256, 128, 64, 32 that divides
+// Cout and still gives at least one CTA per SM (else 32).  0 when the shape is not
+// taken.
+int tc_bn(int N, int H, int W, int Cout, int& BW, int& BH)
+{
+    BW = W < 128 ? W : 128;
+    if (128 % BW != 0 || W % BW != 0) return 0;
+    BH = 128 / BW;
+    if (H % BH != 0) return 0;
+    const long long mtiles = (long long)N * (H / BH) * (W / BW);
+    for (int bn = 256; bn > 32; bn /= 2)
+        if (Cout % bn == 0 && mtiles * (Cout / bn) >= 152) return bn;
+    return 32;
+}
+
+// The tcgen05 convolution for 16-byte aligned tensors of a shape tc_bn takes; returns
+// false (nothing launched) otherwise.
+template <int BN>
+bool launch_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, const float* bias, int Cout, int relu,
+               bf16* y, cudaStream_t s, int BW, int BH)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    CUtensorMap mx, mw;
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+        cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+        cuuint32_t box[4] = {(cuuint32_t)kTcK, (cuuint32_t)BW, (cuuint32_t)BH, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)x, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return false;
+    }
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)9 * Cout};
+        cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
+        cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)BN};
+        cuuint32_t es[2] = {1, 1};
+        if (fn(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wt, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+            return false;
+    }
+    const int smem = kTcStages * (kTcABytes + BN * kTcK * 2) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_conv3x3_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        attr = true;
+    }
+    dim3 grd(N * (H / BH) * (W / BW), Cout / BN);
+    k_conv3x3_tc<BN><<<grd, 128, smem, s>>>(mx, mw, H, W, Cin, Cout, BW, BH, bias, relu, y);
+    return true;
+}
+
+bool conv_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, const float* bias, int Cout, int relu,
+             bf16* y, cudaStream_t s)
+{
+    int BW = 0, BH = 0;
+    const int bn = tc_bn(N, H, W, Cout, BW, BH);
+    if (!bn || (((uintptr_t)x | (uintptr_t)wt | (uintptr_t)y) & 15)) return false;
+    switch (bn) {
+    case 256: return launch_tc<256>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    case 128: return launch_tc<128>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    case 64: return launch_tc<64>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    default: return launch_tc<32>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -417,6 +702,8 @@ int tpfnet_conv3x3(const void* x, int N, int H, int W, int Cin, const void* wt, 
 {
     if (!x || !wt || !y || N < 1 || H < 1 || W < 1 || Cin % kKC || Cout % 32) return TPF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (conv_tc((const bf16*)x, N, H, W, Cin, (const bf16*)wt, bias, Cout, relu, (bf16*)y, s))
+        return status(cudaGetLastError());
     const int wblocks = (W + kBM - 1) / kBM;
     if (Cout % 64 == 0) {
         dim3 grd(wblocks * N * H, Cout / 64);
@@ -426,6 +713,20 @@ int tpfnet_conv3x3(const void* x, int N, int H, int W, int Cin, const void* wt, 
         k_conv3x3<32><<<grd, 128, 0, s>>>((const bf16*)x, N, H, W, Cin, (const bf16*)wt, bias, Cout, relu, (bf16*)y);
     }
     return status(cudaGetLastError());
+}
+
+int tpfnet_conv3x3_tcgen05(int N, int H, int W, int Cin, int Cout)
+{
+    int BW = 0, BH = 0;
+    if (N < 1 || H < 1 || W < 1 || Cin % kKC || Cout % 32 || !encode_fn()) return 0;
+    return tc_bn(N, H, W, Cout, BW, BH);
+}
+
+int tpfnet_status(void)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof(int)) != cudaSuccess) return TPF_ERR_CUDA;
+    return v ? TPF_ERR_TIMEOUT : TPF_OK;
 }
 
 int tpfnet_conv3x3_dgrad(const void* dz, int N, int H, int W, int Cout, const void* wt, int Cin, void* wflip, void* dx,
