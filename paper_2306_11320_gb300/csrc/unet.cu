@@ -118,8 +118,9 @@ k_conv3x3(const bf16* __restrict__ x, int N, int H, int W, int Cin, const bf16* 
 //
 // The same convolution on the fifth-generation tensor cores: an implicit GEMM with
 // M = 128 output pixels (a BW x BH block of one image, BW * BH = 128), N = BN output
-// channels and K = 9 taps x Cin.  Operands are staged by TMA in 64-byte-swizzled
-// K-major tiles (32 channels, 64 bytes, per row): the activation tile of a tap is the
+// channels and K = 9 taps x Cin.  Operands are staged by TMA in swizzled K-major tiles
+// of KC channels per row (64 channels: 128-byte rows and swizzle when Cin allows, else
+// 32 channels: 64-byte rows and swizzle): the activation tile of a tap is the
 // pixel block shifted by (dh, dw), read through a 4-D tensor map whose out-of-range
 // rows and columns come back as zeros (the padding); the weight tile is BN rows of
 // [9 Cout][Cin].  One thread issues the copies into a ring of kTcStages stages, one
@@ -129,8 +130,6 @@ k_conv3x3(const bf16* __restrict__ x, int N, int H, int W, int Cin, const bf16* 
 // apply the ReLU and store bf16.  Every wait is bounded; a wait that runs out sets
 // the error flag and the CTA still releases its tensor memory.
 constexpr int kTcStages = 4;
-constexpr int kTcK = 32;                     // channels per stage (64-byte rows)
-constexpr int kTcABytes = 128 * kTcK * 2;    // activation tile per stage
 __device__ int g_tc_err;                     // a bounded wait of the tcgen05 kernel ran out
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -172,12 +171,16 @@ __device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* m, uint64_t
         "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(sa(b))
         : "memory");
 }
-// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes
-// apart (start address and strides in 16-byte units; descriptor version 1)
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr)
+// shared-memory matrix descriptor of a K-major tile with KC bf16 (2 KC bytes) per row,
+// swizzled over the row width (64 bytes: mode 4, 128 bytes: mode 2), 8-row groups
+// 16 KC bytes apart (start address and strides in 16-byte units; descriptor version 1)
+template <int KC>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t addr)
 {
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+    static_assert(KC == 32 || KC == 64, "64- or 128-byte rows");
+    constexpr uint64_t mode = KC == 64 ? 2 : 4;
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(16 * KC >> 4) << 32) |
+           ((uint64_t)1 << 46) | (mode << 61);
 }
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
 __host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
@@ -187,14 +190,14 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <int BN>
+template <int BN, int KC>
 __global__ void __launch_bounds__(128, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw, int H, int W, int Cin,
              int Cout, int BW, int BH, const float* __restrict__ bias, int relu, bf16* __restrict__ y)
 {
     static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "TMEM columns: a power of two from 32");
-    constexpr int kBBytes = BN * kTcK * 2;
-    constexpr int kStage = kTcABytes + kBBytes;  // multiple of 1024
+    constexpr int kABytes = 128 * KC * 2, kBBytes = BN * KC * 2;
+    constexpr int kStage = kABytes + kBBytes;  // multiple of 1024
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
     __shared__ uint32_t tmem_base;
@@ -205,7 +208,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUt
     const int n = blockIdx.x / bpi, rem = blockIdx.x % bpi;
     const int h0 = (rem / bpr) * BH, w0 = (rem % bpr) * BW;
     const int co0 = blockIdx.y * BN;
-    const int kc = Cin / kTcK, ksteps = 9 * kc;
+    const int kc = Cin / KC, ksteps = 9 * kc;
 
     if (tid == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -233,10 +236,10 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUt
             const int s = k % kTcStages;
             if (k >= kTcStages && !mb_wait(&empty[s], ((k / kTcStages) - 1) & 1)) break;
             unsigned char* a = st0 + s * kStage;
-            const int tap = k / kc, c0 = (k % kc) * kTcK;
+            const int tap = k / kc, c0 = (k % kc) * KC;
             mb_expect_tx(&full[s], kStage);
             tma_4d(a, &mx, &full[s], c0, w0 + tap % 3 - 1, h0 + tap / 3 - 1, n);
-            tma_2d(a + kTcABytes, &mw, &full[s], c0, tap * Cout + co0);
+            tma_2d(a + kABytes, &mw, &full[s], c0, tap * Cout + co0);
             issued = k + 1;
         }
         // copies still in flight (only after a wait ran out) land before the CTA ends
@@ -249,10 +252,10 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUt
             const int s = k % kTcStages;
             if (!mb_wait(&full[s], (k / kTcStages) & 1)) break;
             tc_fence_after();
-            const uint32_t a = sa(st0 + s * kStage), b = a + kTcABytes;
+            const uint32_t a = sa(st0 + s * kStage), b = a + kABytes;
 #pragma unroll
-            for (int kk = 0; kk < kTcK / 16; ++kk) {
-                const uint64_t ad = sw64_desc(a + 32 * kk), bd = sw64_desc(b + 32 * kk);
+            for (int kk = 0; kk < KC / 16; ++kk) {
+                const uint64_t ad = kmajor_desc<KC>(a + 32 * kk), bd = kmajor_desc<KC>(b + 32 * kk);
                 const uint32_t acc = (k | kk) != 0;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -638,7 +641,7 @@ int tc_bn(int N, int H, int W, int Cout, int& BW, int& BH)
 
 // The tcgen05 convolution for 16-byte aligned tensors of a shape tc_bn takes; returns
 // false (nothing launched) otherwise.
-template <int BN>
+template <int BN, int KC>
 bool launch_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, const float* bias, int Cout, int relu,
                bf16* y, cudaStream_t s, int BW, int BH)
 {
@@ -648,34 +651,35 @@ bool launch_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, cons
     {
         cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
         cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
-        cuuint32_t box[4] = {(cuuint32_t)kTcK, (cuuint32_t)BW, (cuuint32_t)BH, 1};
+        cuuint32_t box[4] = {(cuuint32_t)KC, (cuuint32_t)BW, (cuuint32_t)BH, 1};
         cuuint32_t es[4] = {1, 1, 1, 1};
         if (fn(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)x, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+               KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
             CUDA_SUCCESS)
             return false;
     }
     {
         cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)9 * Cout};
         cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
-        cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)BN};
+        cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)BN};
         cuuint32_t es[2] = {1, 1};
         if (fn(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wt, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+               KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
             CUDA_SUCCESS)
             return false;
     }
-    const int smem = kTcStages * (kTcABytes + BN * kTcK * 2) + 1024;
+    const int smem = kTcStages * (128 + BN) * KC * 2 + 1024;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_conv3x3_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        if (cudaFuncSetAttribute(k_conv3x3_tc<BN, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess) {
             cudaGetLastError();
             return false;
         }
         attr = true;
     }
     dim3 grd(N * (H / BH) * (W / BW), Cout / BN);
-    k_conv3x3_tc<BN><<<grd, 128, smem, s>>>(mx, mw, H, W, Cin, Cout, BW, BH, bias, relu, y);
+    k_conv3x3_tc<BN, KC><<<grd, 128, smem, s>>>(mx, mw, H, W, Cin, Cout, BW, BH, bias, relu, y);
     return true;
 }
 
@@ -685,11 +689,19 @@ bool conv_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, const 
     int BW = 0, BH = 0;
     const int bn = tc_bn(N, H, W, Cout, BW, BH);
     if (!bn || (((uintptr_t)x | (uintptr_t)wt | (uintptr_t)y) & 15)) return false;
+    if (Cin % 64 == 0) {
+        switch (bn) {
+        case 256: return launch_tc<256, 64>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+        case 128: return launch_tc<128, 64>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+        case 64: return launch_tc<64, 64>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+        default: return launch_tc<32, 64>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+        }
+    }
     switch (bn) {
-    case 256: return launch_tc<256>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
-    case 128: return launch_tc<128>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
-    case 64: return launch_tc<64>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
-    default: return launch_tc<32>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    case 256: return launch_tc<256, 32>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    case 128: return launch_tc<128, 32>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    case 64: return launch_tc<64, 32>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
+    default: return launch_tc<32, 32>(x, N, H, W, Cin, wt, bias, Cout, relu, y, s, BW, BH);
     }
 }
 

@@ -57,17 +57,17 @@ def _close_bf16(got, ref, relu=False):
 
 
 # (2, 6, 80, ...) and (1, 3, 8, ...) take the mma.sync kernel; the others the tcgen05 one,
-# with every tile width (256, 128, 64 and 32 output channels: the last five rows) and
-# pixel block (128 x 1, 64 x 2, 32 x 4, 16 x 8)
-CONV_SHAPES = [(2, 6, 80, 64, 96), (1, 3, 8, 96, 64), (1, 152, 128, 32, 256), (2, 76, 128, 64, 128),
-               (1, 38, 512, 32, 64), (1, 4, 64, 32, 128), (1, 2, 128, 32, 32), (2, 2, 128, 96, 96),
-               (2, 4, 32, 128, 128), (1, 8, 16, 256, 32)]
+# with every tile width (256, 128, 64 and 32 output channels), both channel chunks
+# (64 when Cin allows it, else 32) and every pixel block (128 x 1, 64 x 2, 32 x 4, 16 x 8)
+CONV_SHAPES = [(2, 6, 80, 64, 96), (1, 3, 8, 96, 64), (1, 152, 128, 32, 256), (1, 152, 128, 64, 256),
+               (2, 76, 128, 64, 128), (1, 38, 512, 32, 64), (1, 38, 512, 64, 64), (1, 4, 64, 32, 128),
+               (1, 2, 128, 32, 32), (2, 2, 128, 96, 96), (2, 4, 32, 128, 128), (1, 8, 16, 256, 32)]
 
 
 def test_conv3x3_kernel_choice():
     lib = _lib()
     choice = [lib.tpfnet_conv3x3_tcgen05(N, H, W, Cin, Cout) for N, H, W, Cin, Cout in CONV_SHAPES]
-    assert choice == [0, 0, 256, 128, 64, 32, 32, 32, 32, 32]
+    assert choice == [0, 0, 256, 256, 128, 64, 64, 32, 32, 32, 32, 32]
     # the network's layers: the widest tile that still gives one CTA per SM
     assert lib.tpfnet_conv3x3_tcgen05(4, 128, 512, 96, 32) == 32
     assert lib.tpfnet_conv3x3_tcgen05(4, 64, 256, 64, 64) == 64
