@@ -34,7 +34,13 @@ int tpfnet_conv3x3(const void *x, int N, int H, int W, int Cin, const void *wt, 
  * tensor memory. */
 int tpfnet_conv3x3_tcgen05(int N, int H, int W, int Cin, int Cout);
 
-/* TPF_OK, or TPF_ERR_TIMEOUT once a bounded wait of the tcgen05 convolution has run
+/* 1 when tpfnet_conv3x3_wgrad runs the tcgen05 kernel for a shape (W a multiple of 64,
+ * 16-byte aligned tensors), 0 for the mma.sync kernel.  The tcgen05 weight gradient
+ * reduces over pixels with both operands staged MN-major by TMA (one pixel's channels
+ * per 128-byte row) and adds each CTA's FP32 partial sums into dw with atomics. */
+int tpfnet_conv3x3_wgrad_tcgen05(int N, int H, int W, int Cin, int Cout);
+
+/* TPF_OK, or TPF_ERR_TIMEOUT once a bounded wait of a tcgen05 kernel has run
  * out in this process (its output is then not to be trusted; the flag stays set);
  * TPF_ERR_CUDA if the flag cannot be read.  Synchronises with the device. */
 int tpfnet_status(void);

@@ -397,6 +397,150 @@ k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dz, int N, 
     if (do_bias && tid < WM) atomicAdd(db + co0 + tid, bacc);
 }
 
+// ------------------------------------------------ tcgen05 weight gradient
+//
+// dW[tap][co][ci] += sum_p dz[p][co] x[p + off(tap)][ci] as GEMMs with M = 128 output
+// channels (co), N = 64 input channels (ci) and K = pixels, one tap per CTA and a
+// range of 64-pixel row segments (split over CTAs, partial sums added with FP32
+// atomics).  The reduction runs over pixels, which NHWC stores outermost, so both
+// operands are staged MN-major: a TMA box of 64 channels (128 bytes, 128-byte
+// swizzle) by 64 pixels puts one pixel's channels in each 128-byte row.  A is two such
+// boxes of dz (co0 and co0 + 64), B one box of x at the tap's shifted pixels
+// (w0 + dw, h + dh), whose out-of-range pixels and channels arrive as zeros (the
+// padding, and the channels past Cin or Cout).  The tap's shift is on the pixel
+// coordinates, never on the innermost (channel) one, so every copy starts on a
+// 16-byte boundary.  Same roles as the forward kernel: one thread copies, one thread
+// issues tcgen05.mma (FP32 accumulator in 64 TMEM columns), four warps read TMEM and
+// add into dW.
+constexpr int kWgStages = 4;
+constexpr int kWgPix = 64;  // pixels per K step (one row segment)
+
+// shared-memory matrix descriptor of an MN-major tile: 128-byte rows of 64 bf16 along
+// M (or N), one row per K index, 128-byte swizzle; blocks of 64 along M lbo bytes
+// apart, groups of 8 rows 1024 bytes apart (descriptor version 1)
+__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t addr, uint32_t lbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__global__ void __launch_bounds__(128, 1)
+k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constant__ CUtensorMap mx, int N, int H,
+                   int W, int Cin, int Cout, int chunks_per_cta, float* __restrict__ dw)
+{
+    constexpr int kBlk = kWgPix * 128;      // one 64-channel x 64-pixel box
+    constexpr int kStage = 3 * kBlk;        // A: two boxes (128 co), B: one box (64 ci)
+    // MN-major A and B (transpose bits), FP32 accumulator, BF16 operands, M 128, N 64
+    constexpr uint32_t idesc = tc_idesc(128, 64) | (1u << 15) | (1u << 16);
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t full[kWgStages], empty[kWgStages], done;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* st0 = tsm + ((1024 - (sa(tsm) & 1023)) & 1023);
+    const int co0 = blockIdx.x * 128, ci0 = blockIdx.y * 64;
+    const int tap = blockIdx.z % 9, split = blockIdx.z / 9;
+    const int dh = tap / 3 - 1, dwd = tap % 3 - 1;
+    const int segs = W / kWgPix, nchunks = N * H * segs;
+    const int c_begin = split * chunks_per_cta;
+    const int c_end = min(c_begin + chunks_per_cta, nchunks);
+    const int ksteps = c_end > c_begin ? c_end - c_begin : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], 1);
+        }
+        mb_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_base)),
+                     "r"(64)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int k = 0; k < ksteps; ++k) {
+            const int s = k % kWgStages;
+            if (k >= kWgStages && !mb_wait(&empty[s], ((k / kWgStages) - 1) & 1)) break;
+            const int c = c_begin + k, row = c / segs;  // row = n * H + h
+            const int w0 = (c - row * segs) * kWgPix, n = row / H, h = row - n * H;
+            unsigned char* a = st0 + s * kStage;
+            mb_expect_tx(&full[s], kStage);
+            tma_4d(a, &mdz, &full[s], co0, w0, h, n);
+            tma_4d(a + kBlk, &mdz, &full[s], co0 + 64, w0, h, n);
+            tma_4d(a + 2 * kBlk, &mx, &full[s], ci0, w0 + dwd, h + dh, n);
+            issued = k + 1;
+        }
+        for (int k = issued > kWgStages ? issued - kWgStages : 0; k < issued; ++k)
+            mb_wait(&full[k % kWgStages], (k / kWgStages) & 1);
+    } else if (warp == 1 && lane == 0) {
+        for (int k = 0; k < ksteps; ++k) {
+            const int s = k % kWgStages;
+            if (!mb_wait(&full[s], (k / kWgStages) & 1)) break;
+            tc_fence_after();
+            const uint32_t a = sa(st0 + s * kStage), b = a + 2 * kBlk;
+#pragma unroll
+            for (int kk = 0; kk < kWgPix / 16; ++kk) {
+                // 16 K rows = two 8-row groups
+                const uint64_t ad = mnmajor_desc(a + 2048 * kk, kBlk), bd = mnmajor_desc(b + 2048 * kk, kBlk);
+                const uint32_t acc = (k | kk) != 0;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             sa(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(&done))
+                     : "memory");
+    }
+    __syncwarp();
+
+    // thread (warp w, lane l) owns output channel co0 + 32 w + l (TMEM lane 32 w + l)
+    mb_wait(&done, 0);
+    tc_fence_after();
+    const int co = co0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < 64; c += 8) {
+        uint32_t r[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (ksteps > 0 && co < Cout) {
+            float* dst = dw + ((size_t)tap * Cout + co) * Cin + ci0 + c;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (ci0 + c + j < Cin) atomicAdd(dst + j, __uint_as_float(r[j]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
+}
+
+// db[co] += sum_p dz[p][co]: one thread per channel per pixel range
+__global__ void k_bias_grad(const bf16* __restrict__ dz, long long P, int Cout, long long per, float* __restrict__ db)
+{
+    const int co = blockIdx.x * blockDim.x + threadIdx.x;
+    if (co >= Cout) return;
+    const long long p0 = (long long)blockIdx.y * per, p1 = p0 + per < P ? p0 + per : P;
+    float acc = 0.f;
+    for (long long p = p0; p < p1; ++p) acc += __bfloat162float(dz[p * Cout + co]);
+    atomicAdd(db + co, acc);
+}
+
 // flipped transpose for the data gradient: wd[tap][ci][co] = w[8 - tap][co][ci]
 __global__ void k_flip_weights(const bf16* __restrict__ w, int Cin, int Cout, bf16* __restrict__ wd)
 {
@@ -705,6 +849,54 @@ bool conv_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, const 
     }
 }
 
+// The tcgen05 weight gradient for W a multiple of 64 and 16-byte aligned tensors;
+// false (nothing launched) otherwise.  Adds into dw (and db).
+bool wgrad_tc(const bf16* x, const bf16* dz, int N, int H, int W, int Cin, int Cout, float* dw, float* db,
+              cudaStream_t s)
+{
+    if (W % kWgPix != 0 || (((uintptr_t)x | (uintptr_t)dz) & 15)) return false;
+    auto fn = encode_fn();
+    if (!fn) return false;
+    CUtensorMap mdz, mx;
+    auto make = [&](CUtensorMap* m, const bf16* base, int C) {
+        cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+        cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+        cuuint32_t box[4] = {64, (cuuint32_t)kWgPix, 1, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!make(&mdz, dz, Cout) || !make(&mx, x, Cin)) return false;
+    const int smem = kWgStages * 3 * kWgPix * 128 + 1024;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        attr = true;
+    }
+    // split the pixel segments so that the grid fills the GPU about twice
+    const long long nchunks = (long long)N * H * (W / kWgPix);
+    const int ctiles = (Cout + 127) / 128, itiles = (Cin + 63) / 64;
+    const long long base = 9LL * ctiles * itiles;
+    long long splits = (2 * 152 + base - 1) / base;
+    if (splits > nchunks) splits = nchunks;
+    if (splits < 1) splits = 1;
+    const long long per = (nchunks + splits - 1) / splits;
+    splits = (nchunks + per - 1) / per;
+    dim3 grd(ctiles, itiles, 9 * (unsigned)splits);
+    k_conv3x3_wgrad_tc<<<grd, 128, smem, s>>>(mdz, mx, N, H, W, Cin, Cout, (int)per, dw);
+    if (db) {
+        const long long P = (long long)N * H * W;
+        const long long ys = P < 256 ? P : 256, pper = (P + ys - 1) / ys;
+        k_bias_grad<<<dim3((Cout + 127) / 128, (unsigned)((P + pper - 1) / pper)), 128, 0, s>>>(dz, P, Cout, pper, db);
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -734,6 +926,11 @@ int tpfnet_conv3x3_tcgen05(int N, int H, int W, int Cin, int Cout)
     return tc_bn(N, H, W, Cout, BW, BH);
 }
 
+int tpfnet_conv3x3_wgrad_tcgen05(int N, int H, int W, int Cin, int Cout)
+{
+    return N >= 1 && H >= 1 && W >= 1 && Cin % 32 == 0 && Cout % 32 == 0 && W % kWgPix == 0 && encode_fn() ? 1 : 0;
+}
+
 int tpfnet_status(void)
 {
     int v = 0;
@@ -756,6 +953,8 @@ int tpfnet_conv3x3_wgrad(const void* x, const void* dz, int N, int H, int W, int
                          void* stream)
 {
     if (!x || !dz || !dw || Cin % kWN || Cout % 32) return TPF_ERR_INVALID_ARG;
+    if (wgrad_tc((const bf16*)x, (const bf16*)dz, N, H, W, Cin, Cout, dw, db, (cudaStream_t)stream))
+        return status(cudaGetLastError());
     const int WM = Cout % 64 == 0 ? 64 : 32;
     const long long P = (long long)N * H * W;
     // split the pixels so that the grid fills the GPU a few times over

@@ -23,6 +23,7 @@ _fp, _dp = C.POINTER(C.c_float), C.POINTER(C.c_double)
 SIGNATURES = {
     "tpfnet_conv3x3": [_vp, _ip, _ip, _ip, _ip, _vp, _vp, _ip, _ip, _vp, _vp],
     "tpfnet_conv3x3_tcgen05": [_ip, _ip, _ip, _ip, _ip],
+    "tpfnet_conv3x3_wgrad_tcgen05": [_ip, _ip, _ip, _ip, _ip],
     "tpfnet_status": [],
     "tpfnet_conv3x3_dgrad": [_vp, _ip, _ip, _ip, _ip, _vp, _ip, _vp, _vp, _vp],
     "tpfnet_conv3x3_wgrad": [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _vp, _vp, _vp],

@@ -95,7 +95,18 @@ def test_conv3x3_forward(N, H, W, Cin, Cout, relu):
     _close_bf16(_np(y), ref)
 
 
-@pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 6, 80, 64, 96), (1, 5, 16, 32, 64)])
+# the weight gradient of the first two shapes runs on mma.sync, of the others on tcgen05
+# (W a multiple of 64; channel counts below, at and above one 64-channel box)
+GRAD_SHAPES = [(2, 6, 80, 64, 96), (1, 5, 16, 32, 64), (1, 3, 64, 32, 32), (2, 2, 128, 96, 64),
+               (1, 2, 64, 256, 160), (1, 4, 128, 64, 128)]
+
+
+def test_wgrad_kernel_choice():
+    lib = _lib()
+    assert [lib.tpfnet_conv3x3_wgrad_tcgen05(*sh) for sh in GRAD_SHAPES] == [0, 0, 1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("N,H,W,Cin,Cout", GRAD_SHAPES)
 def test_conv3x3_data_and_weight_gradients(N, H, W, Cin, Cout):
     rng = np.random.default_rng(7 + W)
     lib, s = _lib(), C.c_void_p(torch.cuda.current_stream().cuda_stream)
