@@ -472,9 +472,12 @@ k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constan
             const int c = c_begin + k, row = c / segs;  // row = n * H + h
             const int w0 = (c - row * segs) * kWgPix, n = row / H, h = row - n * H;
             unsigned char* a = st0 + s * kStage;
-            mb_expect_tx(&full[s], kStage);
+            // the second dz box only when it holds channels: otherwise TMEM lanes 64-127
+            // accumulate whatever that smem holds and are never read
+            const bool a2 = co0 + 64 < Cout;
+            mb_expect_tx(&full[s], a2 ? kStage : 2 * kBlk);
             tma_4d(a, &mdz, &full[s], co0, w0, h, n);
-            tma_4d(a + kBlk, &mdz, &full[s], co0 + 64, w0, h, n);
+            if (a2) tma_4d(a + kBlk, &mdz, &full[s], co0 + 64, w0, h, n);
             tma_4d(a + 2 * kBlk, &mx, &full[s], ci0, w0 + dwd, h + dh, n);
             issued = k + 1;
         }
