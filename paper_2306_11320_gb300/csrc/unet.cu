@@ -816,14 +816,10 @@ bool launch_tc(const bf16* x, int N, int H, int W, int Cin, const bf16* wt, cons
             return false;
     }
     const int smem = kTcStages * (128 + BN) * KC * 2 + 1024;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_conv3x3_tc<BN, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        attr = true;
+    // set on every call: the attribute belongs to the current device
+    if (cudaFuncSetAttribute(k_conv3x3_tc<BN, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
     dim3 grd(N * (H / BH) * (W / BW), Cout / BN);
     k_conv3x3_tc<BN, KC><<<grd, 128, smem, s>>>(mx, mw, H, W, Cin, Cout, BW, BH, bias, relu, y);
@@ -872,14 +868,9 @@ bool wgrad_tc(const bf16* x, const bf16* dz, int N, int H, int W, int Cin, int C
     };
     if (!make(&mdz, dz, Cout) || !make(&mx, x, Cin)) return false;
     const int smem = kWgStages * 3 * kWgPix * 128 + 1024;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        attr = true;
+    if (cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
     // split the pixel segments so that the grid fills the GPU about twice
     const long long nchunks = (long long)N * H * (W / kWgPix);
