@@ -147,6 +147,20 @@ int tpflbm_step(tpflbm_t h, long long nsteps);
  * the stream. */
 int tpflbm_status(tpflbm_t h);
 
+/* The same report without waiting: enqueue a copy of the step kernels' 4-byte error
+ * flag into *flag (host memory the caller owns; page-locked for the copy to be
+ * asynchronous), ordered after the steps enqueued so far, and return.  copy_stream
+ * (cudaStream_t) NULL or the handle's stream: the copy is enqueued on the handle's
+ * stream, and later steps queue behind it.  Another stream: the copy is enqueued there
+ * behind an event recorded on the handle's stream, and later steps do not wait for it
+ * (the flag may then also include a failure of a step enqueued after the call).  Once
+ * the copy's stream has passed it (an event recorded there after this call, or any
+ * later synchronisation), *flag is 0 if every step enqueued before the call completed
+ * and nonzero if a step kernel gave up waiting for its copies.  Lets a caller read
+ * each step's outcome while the next steps run.  TPF_OK, or TPF_ERR_CUDA if the copy
+ * cannot be enqueued. */
+int tpflbm_status_async(tpflbm_t h, int *flag, void *copy_stream);
+
 /* Macroscopic fields of the current state, as the next step computes them:
  * phi = sum f_i, T = sum h_i, u from rho u = sum c_i g_i + (Fs + G)/2 and p from the
  * pressure moment of Sec. 3.1.  Each output is a caller-owned [ny][nx] float32

@@ -46,6 +46,8 @@ struct tpflbm {
     int2* tiles = nullptr;              // (x0, y0) of the TMA tiles in the order the kernel walks them
     // CUDA graphs of kGraphSteps steps starting from pop[0] / pop[1] (captured on first use)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // marks the steps enqueued so far for tpflbm_status_async's copy stream (created on first use)
+    cudaEvent_t status_ev = nullptr;
     long long t = 0;
     std::string err_msg;
 };

@@ -970,6 +970,23 @@ int tpflbm_status(tpflbm_t h)
     return check_err(h);
 }
 
+int tpflbm_status_async(tpflbm_t h, int* flag, void* copy_stream)
+{
+    if (!h || !flag) return TPF_ERR_INVALID_ARG;
+    cudaStream_t cs = (cudaStream_t)copy_stream;
+    if (!cs || cs == h->stream) {
+        TPF_CUDA(h, cudaMemcpyAsync(flag, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        return TPF_OK;
+    }
+    // on the copy stream, behind an event on the handle's stream: the next steps do not
+    // wait for the copy
+    if (!h->status_ev) TPF_CUDA(h, cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming));
+    TPF_CUDA(h, cudaEventRecord(h->status_ev, h->stream));
+    TPF_CUDA(h, cudaStreamWaitEvent(cs, h->status_ev, 0));
+    TPF_CUDA(h, cudaMemcpyAsync(flag, h->err, sizeof(int), cudaMemcpyDeviceToHost, cs));
+    return TPF_OK;
+}
+
 int tpflbm_get_fields(tpflbm_t h, float* phi, float* ux, float* uy, float* p, float* T)
 {
     if (!h) return TPF_ERR_INVALID_ARG;
@@ -1315,6 +1332,7 @@ void tpflbm_destroy(tpflbm_t h)
     if (!h) return;
     for (int c = 0; c < 2; ++c)
         if (h->graph[c]) cudaGraphExecDestroy(h->graph[c]);
+    if (h->status_ev) cudaEventDestroy(h->status_ev);
     if (h->owns && h->ws) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->ws);

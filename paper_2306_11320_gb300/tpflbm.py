@@ -57,6 +57,7 @@ SIGNATURES = {
     "tpflbm_init_forced": ([_vp, _vp, _vp, _vp, _vp, _vp, _ip], _ip),
     "tpflbm_step": ([_vp, C.c_longlong], _ip),
     "tpflbm_status": ([_vp], _ip),
+    "tpflbm_status_async": ([_vp, _vp, _vp], _ip),
     "tpflbm_get_fields": ([_vp, _vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_get_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
     "tpflbm_set_state": ([_vp, _vp, _vp, _vp, _vp], _ip),
