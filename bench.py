@@ -194,15 +194,20 @@ def bench_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# step cap of the time-to-steady runs: every cold and warm run of the 20 held-out channels
+# converges within 1.47M steps, so the cap only guards against a run that never does
+STEADY_MAX_STEPS = 2_000_000
+
+
 def time_to_steady(instances=None, log=lambda m: None):
     """Cold against learned warm start on the held-out warm-start channels (512 x 128
     heated microchannel), wall time to max(r_u, r_T) < 1e-8 with r every RESID_K steps,
-    at most 800k steps; returns (rows, summary) of warmstart.compare/summarize."""
+    at most STEADY_MAX_STEPS steps; returns (rows, summary) of warmstart.compare/summarize."""
     from paper_2306_11320_gb300 import warmstart as WS
 
     net, norm, meta = WS.load(WS.WEIGHTS)
     insts = WS.held_out(meta, instances)
-    rows = WS.compare(net, norm, insts, tols=(1e-8,), max_steps=800_000, log=log)
+    rows = WS.compare(net, norm, insts, tols=(1e-8,), max_steps=STEADY_MAX_STEPS, log=log)
     return rows, WS.summarize(rows, (1e-8,)), meta
 
 
@@ -318,7 +323,7 @@ def bench_ours(args, rank, world, local_rank):
         # the metric's second half: time to steady state, plain against learned warm start
         rows, summ, meta = time_to_steady()
         agg = summ["aggregate_1e-08"]
-        steady = {"workload": "warmstart_512x128", "instances": len(rows), "tol": 1e-8, "max_steps": 800_000,
+        steady = {"workload": "warmstart_512x128", "instances": len(rows), "tol": 1e-8, "max_steps": STEADY_MAX_STEPS,
                   "cold_s": agg["cold_s"], "warm_s": agg["warm_s"], "ratio": agg["ratio"],
                   "cold_unconverged": agg["cold_unconverged"], "warm_unconverged": agg["warm_unconverged"],
                   "per_instance_median": summ["speedup_time_1e-08"]["median"], "target": ">= 3x",
@@ -428,7 +433,7 @@ def bench_warmstart(args, rank, world, local_rank):
     from paper_2306_11320_gb300 import warmstart as WS
 
     torch.cuda.set_device(local_rank)
-    tol, max_steps = 1e-8, 800_000
+    tol, max_steps = 1e-8, STEADY_MAX_STEPS
     with ClockSampler(local_rank) as clk:
         rows, summ, meta = time_to_steady(args.instances)
     insts = rows
