@@ -400,9 +400,10 @@ k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dz, int N, 
 // ------------------------------------------------ tcgen05 weight gradient
 //
 // dW[tap][co][ci] += sum_p dz[p][co] x[p + off(tap)][ci] as GEMMs with M = 128 output
-// channels (co), N = 64 input channels (ci) and K = pixels, one tap per CTA and a
-// range of 64-pixel row segments (split over CTAs, partial sums added with FP32
-// atomics).  The reduction runs over pixels, which NHWC stores outermost, so both
+// channels (co), N = 64 input channels (ci) and K = pixels, over a range of 64-pixel
+// row segments per CTA (split over CTAs, partial sums added with FP32 atomics), for one
+// tap or for the three taps of one column offset, which share each dz box (one 64-column
+// TMEM accumulator per tap).  The reduction runs over pixels, which NHWC stores outermost, so both
 // operands are staged MN-major: a TMA box of 64 channels (128 bytes, 128-byte
 // swizzle) by 64 pixels puts one pixel's channels in each 128-byte row.  A is two such
 // boxes of dz (co0 and co0 + 64), B one box of x at the tap's shifted pixels
@@ -413,7 +414,10 @@ k_conv3x3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dz, int N, 
 // issues tcgen05.mma (FP32 accumulator in 64 TMEM columns), four warps read TMEM and
 // add into dW.
 constexpr int kWgStages = 4;
-constexpr int kWgPix = 64;  // pixels per K step (one row segment)
+constexpr int kWgPix = 64;   // pixels per K step (one row segment)
+// taps per CTA: one, or the three rows (dh) of one column offset (dw), which share their
+// dz boxes; three measured faster from 2^17 pixels up (the 512 x 128 level), one below
+constexpr long long kWgTaps3Pixels = 1 << 17;
 
 // shared-memory matrix descriptor of an MN-major tile: 128-byte rows of 64 bf16 along
 // M (or N), one row per K index, 128-byte swizzle; blocks of 64 along M lbo bytes
@@ -424,12 +428,15 @@ __device__ __forceinline__ uint64_t mnmajor_desc(uint32_t addr, uint32_t lbo)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+template <int TAPS>
 __global__ void __launch_bounds__(128, 1)
 k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constant__ CUtensorMap mx, int N, int H,
                    int W, int Cin, int Cout, int chunks_per_cta, float* __restrict__ dw)
 {
+    static_assert(TAPS == 1 || TAPS == 3, "one tap, or the three rows of one column offset");
     constexpr int kBlk = kWgPix * 128;      // one 64-channel x 64-pixel box
-    constexpr int kStage = 3 * kBlk;        // A: two boxes (128 co), B: one box (64 ci)
+    constexpr int kStage = (2 + TAPS) * kBlk;  // A: two boxes (128 co), B: one box (64 ci) per tap
+    constexpr uint32_t kCols = TAPS == 1 ? 64 : 256;  // TMEM columns: 64 per tap, a power of two
     // MN-major A and B (transpose bits), FP32 accumulator, BF16 operands, M 128, N 64
     constexpr uint32_t idesc = tc_idesc(128, 64) | (1u << 15) | (1u << 16);
     extern __shared__ __align__(1024) unsigned char tsm[];
@@ -438,8 +445,11 @@ k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constan
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* st0 = tsm + ((1024 - (sa(tsm) & 1023)) & 1023);
     const int co0 = blockIdx.x * 128, ci0 = blockIdx.y * 64;
-    const int tap = blockIdx.z % 9, split = blockIdx.z / 9;
-    const int dh = tap / 3 - 1, dwd = tap % 3 - 1;
+    // TAPS 1: tap = z % 9; TAPS 3: taps dwi, dwi + 3, dwi + 6 (dh = -1, 0, 1) with dwi = z % 3
+    constexpr int kGroups = 9 / TAPS;
+    const int g = blockIdx.z % kGroups, split = blockIdx.z / kGroups;
+    const int tap0 = g;  // the CTA's first tap (dh = -1 when TAPS is 3)
+    const int dwd = tap0 % 3 - 1;
     const int segs = W / kWgPix, nchunks = N * H * segs;
     const int c_begin = split * chunks_per_cta;
     const int c_end = min(c_begin + chunks_per_cta, nchunks);
@@ -455,7 +465,7 @@ k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constan
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_base)),
-                     "r"(64)
+                     "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -475,10 +485,14 @@ k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constan
             // the second dz box only when it holds channels: otherwise TMEM lanes 64-127
             // accumulate whatever that smem holds and are never read
             const bool a2 = co0 + 64 < Cout;
-            mb_expect_tx(&full[s], a2 ? kStage : 2 * kBlk);
+            mb_expect_tx(&full[s], a2 ? kStage : kStage - kBlk);
             tma_4d(a, &mdz, &full[s], co0, w0, h, n);
             if (a2) tma_4d(a + kBlk, &mdz, &full[s], co0 + 64, w0, h, n);
-            tma_4d(a + 2 * kBlk, &mx, &full[s], ci0, w0 + dwd, h + dh, n);
+#pragma unroll
+            for (int t = 0; t < TAPS; ++t) {
+                const int dh = (tap0 + 3 * t) / 3 - 1;
+                tma_4d(a + (2 + t) * kBlk, &mx, &full[s], ci0, w0 + dwd, h + dh, n);
+            }
             issued = k + 1;
         }
         for (int k = issued > kWgStages ? issued - kWgStages : 0; k < issued; ++k)
@@ -488,17 +502,21 @@ k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constan
             const int s = k % kWgStages;
             if (!mb_wait(&full[s], (k / kWgStages) & 1)) break;
             tc_fence_after();
-            const uint32_t a = sa(st0 + s * kStage), b = a + 2 * kBlk;
+            const uint32_t a = sa(st0 + s * kStage);
 #pragma unroll
-            for (int kk = 0; kk < kWgPix / 16; ++kk) {
-                // 16 K rows = two 8-row groups
-                const uint64_t ad = mnmajor_desc(a + 2048 * kk, kBlk), bd = mnmajor_desc(b + 2048 * kk, kBlk);
-                const uint32_t acc = (k | kk) != 0;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+            for (int t = 0; t < TAPS; ++t) {
+                const uint32_t b = a + (2 + t) * kBlk;
+#pragma unroll
+                for (int kk = 0; kk < kWgPix / 16; ++kk) {
+                    // 16 K rows = two 8-row groups
+                    const uint64_t ad = mnmajor_desc(a + 2048 * kk, kBlk), bd = mnmajor_desc(b + 2048 * kk, kBlk);
+                    const uint32_t acc = (k | kk) != 0;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 64 * t),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              sa(&empty[s]))
@@ -514,23 +532,24 @@ k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap mdz, const __grid_constan
     tc_fence_after();
     const int co = co0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int c = 0; c < 64; c += 8) {
+    for (int c = 0; c < 64 * TAPS; c += 8) {
         uint32_t r[8];
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                      : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int tap = tap0 + 3 * (c / 64), cc = c % 64;
         if (ksteps > 0 && co < Cout) {
-            float* dst = dw + ((size_t)tap * Cout + co) * Cin + ci0 + c;
+            float* dst = dw + ((size_t)tap * Cout + co) * Cin + ci0 + cc;
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (ci0 + c + j < Cin) atomicAdd(dst + j, __uint_as_float(r[j]));
+                if (ci0 + cc + j < Cin) atomicAdd(dst + j, __uint_as_float(r[j]));
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
 // db[co] += sum_p dz[p][co]: one thread per channel per pixel range
@@ -867,24 +886,30 @@ bool wgrad_tc(const bf16* x, const bf16* dz, int N, int H, int W, int Cin, int C
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     if (!make(&mdz, dz, Cout) || !make(&mx, x, Cin)) return false;
-    const int smem = kWgStages * 3 * kWgPix * 128 + 1024;
-    if (cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    const long long P = (long long)N * H * W;
+    const int taps = P >= kWgTaps3Pixels ? 3 : 1;
+    const int smem = kWgStages * (2 + taps) * kWgPix * 128 + 1024;
+    if (cudaFuncSetAttribute(taps == 3 ? (const void*)k_conv3x3_wgrad_tc<3> : (const void*)k_conv3x3_wgrad_tc<1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     // split the pixel segments so that the grid fills the GPU about twice
     const long long nchunks = (long long)N * H * (W / kWgPix);
     const int ctiles = (Cout + 127) / 128, itiles = (Cin + 63) / 64;
-    const long long base = 9LL * ctiles * itiles;
-    long long splits = (2 * 152 + base - 1) / base;
+    const long long base = (9 / taps) * (long long)ctiles * itiles;
+    const long long target = taps == 1 ? 2 * 152 : 152;  // CTAs per SM the shared memory allows
+    long long splits = (target + base - 1) / base;
     if (splits > nchunks) splits = nchunks;
     if (splits < 1) splits = 1;
     const long long per = (nchunks + splits - 1) / splits;
     splits = (nchunks + per - 1) / per;
-    dim3 grd(ctiles, itiles, 9 * (unsigned)splits);
-    k_conv3x3_wgrad_tc<<<grd, 128, smem, s>>>(mdz, mx, N, H, W, Cin, Cout, (int)per, dw);
+    dim3 grd(ctiles, itiles, (9 / taps) * (unsigned)splits);
+    if (taps == 3)
+        k_conv3x3_wgrad_tc<3><<<grd, 128, smem, s>>>(mdz, mx, N, H, W, Cin, Cout, (int)per, dw);
+    else
+        k_conv3x3_wgrad_tc<1><<<grd, 128, smem, s>>>(mdz, mx, N, H, W, Cin, Cout, (int)per, dw);
     if (db) {
-        const long long P = (long long)N * H * W;
         const long long ys = P < 256 ? P : 256, pper = (P + ys - 1) / ys;
         k_bias_grad<<<dim3((Cout + 127) / 128, (unsigned)((P + pper - 1) / pper)), 128, 0, s>>>(dz, P, Cout, pper, db);
     }

@@ -97,13 +97,14 @@ def test_conv3x3_forward(N, H, W, Cin, Cout, relu):
 
 # the weight gradient of the first two shapes runs on mma.sync, of the others on tcgen05
 # (W a multiple of 64; channel counts below, at and above one 64-channel box)
+# (the last one has 2^17 pixels: its CTAs take three taps each)
 GRAD_SHAPES = [(2, 6, 80, 64, 96), (1, 5, 16, 32, 64), (1, 3, 64, 32, 32), (2, 2, 128, 96, 64),
-               (1, 2, 64, 256, 160), (1, 4, 128, 64, 128)]
+               (1, 2, 64, 256, 160), (1, 4, 128, 64, 128), (2, 256, 256, 32, 96)]
 
 
 def test_wgrad_kernel_choice():
     lib = _lib()
-    assert [lib.tpfnet_conv3x3_wgrad_tcgen05(*sh) for sh in GRAD_SHAPES] == [0, 0, 1, 1, 1, 1]
+    assert [lib.tpfnet_conv3x3_wgrad_tcgen05(*sh) for sh in GRAD_SHAPES] == [0, 0, 1, 1, 1, 1, 1]
 
 
 @pytest.mark.parametrize("N,H,W,Cin,Cout", GRAD_SHAPES)
