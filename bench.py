@@ -1,7 +1,7 @@
 """Benchmark of the fused coupled-LBM step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--storage fp32|fp16] [--impl ours|reference]
-                [--flush] [--workload bubbles|ensemble|warmstart]
+                [--flush] [--workload bubbles|ensemble|warmstart|unet|cpu]
 
 One step = one pass of the whole hot path (moments, stencils, closures, forces,
 the three collisions, streaming and boundary rules) over the 2048 x 512 bubble
@@ -54,6 +54,14 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def _kernel_hash():
@@ -420,6 +428,105 @@ def bench_ensemble(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# the warm-start U-Net's 3x3 layers at batch 4 (512 x 128 input): N, H, W, Cin, Cout
+UNET_LAYERS = [(4, 128, 512, 32, 32), (4, 64, 256, 64, 64), (4, 32, 128, 128, 128), (4, 16, 64, 256, 256),
+               (4, 32, 128, 384, 128), (4, 64, 256, 192, 64), (4, 128, 512, 96, 32)]
+
+
+def bench_unet(args, rank, world, local_rank):
+    """The warm-start U-Net's tensor-core kernels: per 3x3 layer shape of the network
+    (batch 4), the forward convolution (bias + ReLU), the data gradient and the weight
+    gradient through tpfnet_* (CUDA events, --warmup untimed and min(--steps, 50) timed
+    calls each; FLOP = 2 N H W 9 Cin Cout per call), which kernel each takes, and a whole
+    training step (forward, MSE, backward, Adam) on random data.  The U-Net is off the
+    lattice's measured path; this line documents its kernels."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2306_11320_gb300.unet import UNet, net_library
+
+    torch.cuda.set_device(local_rank)
+    lib = net_library()
+    stream = torch.cuda.current_stream()
+    s = ctypes.c_void_p(stream.cuda_stream)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    peak, peak_kind = _bf16_peak()
+    reps = max(1, min(args.steps, 50))  # calls timed per kernel and shape (the default --steps is for the lattice)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps  # us per call
+
+    layers = []
+    with ClockSampler(local_rank) as clk:
+        for N, H, W, Cin, Cout in UNET_LAYERS:
+            g = torch.Generator(device="cuda").manual_seed(N * H * W + Cin + Cout)
+            x = torch.randn((N, H, W, Cin), device="cuda", generator=g).to(torch.bfloat16)
+            wt = (torch.randn((9, Cout, Cin), device="cuda", generator=g) / (9 * Cin) ** 0.5).to(torch.bfloat16)
+            b = torch.randn(Cout, device="cuda", generator=g)
+            y = torch.empty((N, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+            dz = torch.randn((N, H, W, Cout), device="cuda", generator=g).to(torch.bfloat16)
+            dx = torch.empty((N, H, W, Cin), dtype=torch.bfloat16, device="cuda")
+            wf = torch.empty(9 * Cin * Cout, dtype=torch.bfloat16, device="cuda")
+            dw = torch.zeros((9, Cout, Cin), device="cuda")
+            db = torch.zeros(Cout, device="cuda")
+            flop = 2.0 * N * H * W * 9 * Cin * Cout
+            row = {"shape": [N, H, W, Cin, Cout],
+                   "kernel": {"forward": "tcgen05 BN %d" % lib.tpfnet_conv3x3_tcgen05(N, H, W, Cin, Cout)
+                              if lib.tpfnet_conv3x3_tcgen05(N, H, W, Cin, Cout) else "mma.sync",
+                              "weight_gradient": "tcgen05" if lib.tpfnet_conv3x3_wgrad_tcgen05(N, H, W, Cin, Cout)
+                              else "mma.sync"}}
+            for name, fn in (
+                    ("forward", lambda: lib.tpfnet_conv3x3(P(x), N, H, W, Cin, P(wt), P(b), Cout, 1, P(y), s)),
+                    ("data_gradient", lambda: lib.tpfnet_conv3x3_dgrad(P(dz), N, H, W, Cout, P(wt), Cin, P(wf), P(dx), s)),
+                    ("weight_gradient", lambda: lib.tpfnet_conv3x3_wgrad(P(x), P(dz), N, H, W, Cin, Cout, P(dw), P(db), s))):
+                us = timed(fn)
+                row[name] = {"us": round(us, 2), "tflops": round(flop / us / 1e6, 1),
+                             "frac_of_bf16_peak": round(flop / us / 1e6 / peak, 4)}
+            layers.append(row)
+        net = UNet(4, 4, seed=1)
+        rng = np.random.default_rng(0)
+        xin = torch.from_numpy(rng.standard_normal((4, 128, 512, 32)).astype(np.float32)).to(torch.bfloat16).cuda()
+        tgt = torch.from_numpy(rng.standard_normal((4, 128, 512, 4)).astype(np.float32)).cuda()
+        for _ in range(3):
+            net.train_step(xin, tgt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            net.train_step(xin, tgt)
+        torch.cuda.synchronize()
+        train_ms = (time.perf_counter() - t0) * 1e3 / reps
+    if lib.tpfnet_status() != 0:
+        raise RuntimeError("a tcgen05 kernel's bounded wait ran out")
+    if rank != 0:
+        return
+    tot = {k: sum(r[k]["us"] for r in layers) for k in ("forward", "data_gradient", "weight_gradient")}
+    flops = sum(2.0 * n * h * w * 9 * ci * co for n, h, w, ci, co in UNET_LAYERS)
+    line = {
+        "metric": "U-Net 3x3 convolution TFLOP/s (forward, the network's seven layer shapes)",
+        "value": flops / tot["forward"] / 1e6, "unit": "TFLOP/s", "n_gpus": world, "steps": reps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic", "config": {"workload": "unet_warmstart_layers", "batch": 4},
+        "roofline": {"bound": "tensor", "achieved": flops / tot["forward"] / 1e6, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / tot["forward"] / 1e6 / peak, "peak_source": peak_kind,
+                     "kernel": "k_conv3x3_tc"},
+        "totals_us": {k: round(v, 1) for k, v in tot.items()},
+        "layers": layers,
+        "train_step_ms": round(train_ms, 3),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_warmstart(args, rank, world, local_rank):
     """Time to steady state of the 512 x 128 heated microchannel from the cold start
     and from the trained network's prediction (committed weights), on the held-out
@@ -525,10 +632,11 @@ def main():
                     help="skip the time-to-steady comparison (cold against learned warm start) of the default line")
     ap.add_argument("--flush", action="store_true",
                     help="write 256 MiB between timed steps (per-step events) instead of timing steps back to back")
-    ap.add_argument("--workload", choices=("bubbles", "ensemble", "warmstart", "cpu"), default="bubbles",
+    ap.add_argument("--workload", choices=("bubbles", "ensemble", "warmstart", "unet", "cpu"), default="bubbles",
                     help="bubbles: the 2048x512 channel (the headline line); ensemble: the "
                          "256-lattice parameter sweep through the batched launch; warmstart: time to "
-                         "steady state, cold vs learned warm start, on held-out microchannels; cpu: the "
+                         "steady state, cold vs learned warm start, on held-out microchannels; unet: the "
+                         "warm-start network's tensor-core kernels per layer shape; cpu: the "
                          "FP64 oracle at one thread and at all threads on every workload configuration")
     ap.add_argument("--instances", type=int, default=20, help="warmstart: held-out instances to time")
     ap.add_argument("--collision", choices=("bgk", "trt"), default="bgk",
@@ -555,6 +663,8 @@ def main():
             bench_ensemble(args, rank, world, local_rank)
         elif args.workload == "warmstart":
             bench_warmstart(args, rank, world, local_rank)
+        elif args.workload == "unet":
+            bench_unet(args, rank, world, local_rank)
         else:
             bench_ours(args, rank, world, local_rank)
     finally:
